@@ -1,0 +1,147 @@
+/*
+ * eeid -- squared eigenvector components of real symmetric FP64 matrices through
+ * the eigenvector-eigenvalue identity, on one NVIDIA GB300 (sm_103a) GPU.
+ *
+ * The operation (Sec. 2, Eq. 1 of "Eigenvector Component Calculation Speedup over
+ * NumPy for High-Performance Computing", arXiv 2002.04989): for a real symmetric
+ * n x n matrix A with eigenvalues lam_1(A) <= ... <= lam_n(A) and unit eigenvectors
+ * v_i, and M_j the (n-1) x (n-1) minor of A with row and column j removed,
+ *
+ *     |v_ij|^2 * prod_{k != i} (lam_i(A) - lam_k(A)) = prod_{k=1}^{n-1} (lam_i(A) - lam_k(M_j)).
+ *
+ * The paper's functions take (matrix, i, j) and return one component (Algorithms
+ * 0 and 1, Sec. 3); this library takes whole sets of eigen-indices i ("rows") and
+ * component indices j ("cols") and returns the grid.  Where the printed
+ * algorithms and Eq. 1 disagree (which index is removed for the minor, which
+ * product is the numerator), Eq. 1 is followed.
+ *
+ * Conventions for every entry point:
+ *  - Indices are 0-based.  Eigen-index i = k means the (k+1)-th smallest
+ *    eigenvalue; eigenvalue outputs are ascending.
+ *  - Matrices are row-major FP64 with leading dimension lda >= n (in elements).
+ *    Only the lower triangle (element (r, c), r >= c, at A[r*lda + c]) is read; the
+ *    caller guarantees symmetry.  Entries must be finite.
+ *  - "d_" pointers are device memory of the context's device; "h_" pointers are
+ *    host memory.  The caller owns every buffer it passes; the library never
+ *    frees or retains them beyond the call (asynchronous calls read/write them
+ *    until the stream reaches that point).
+ *  - Calls that take a stream (a cudaStream_t passed as void*; NULL = the legacy
+ *    default stream) are asynchronous: they validate arguments and enqueue work,
+ *    and return EEID_OK once enqueued.  Warnings and device-side errors found
+ *    while the work runs are returned by the next eeid_sync() on that context.
+ *  - A context's workspace is shared by its calls: issue the calls of one
+ *    context on one stream (or order them yourself).  Contexts are not
+ *    thread-safe; use one per host thread.
+ *  - Status codes: negative = error (nothing, or only part, was enqueued),
+ *    positive = warning (results written).  eeid_last_error() gives a message.
+ */
+#ifndef EEID_H
+#define EEID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EEID_OK = 0,
+  /* Two eigenvalues of A are exactly equal: Eq. 1 is 0/0 for those i.  The rows
+   * of the affected eigen-indices are filled with NaN. */
+  EEID_WARN_DEGENERATE = 1,
+  /* The spectrum's minimum relative gap min_k (lam_{k+1}-lam_k)/max|lam| is below
+   * 1e-4: results are computed but lie outside the accuracy contract. */
+  EEID_WARN_SMALL_GAP = 2,
+  EEID_ERR_INVALID = -1,   /* bad argument (NULL pointer, size, index, duplicate) */
+  EEID_ERR_NOMEM = -2,     /* workspace would exceed the context's HBM budget */
+  EEID_ERR_CUDA = -3,      /* a CUDA call failed (message in eeid_last_error) */
+  EEID_ERR_TIMEOUT = -4,   /* a bounded wait ran out */
+  EEID_ERR_BUSY = -5,      /* serving: admission refused (non-blocking submit) */
+  EEID_ERR_NOT_FOUND = -6, /* serving: unknown ticket */
+  EEID_ERR_CANCELLED = -7  /* serving: request cancelled before it ran */
+} eeid_status;
+
+typedef struct eeid_ctx eeid_ctx;
+
+/* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the device
+ * workspace the context may allocate (0 = half of the device's free memory at
+ * creation).  *out receives the context.  Errors: EEID_ERR_INVALID (out NULL,
+ * bad device), EEID_ERR_CUDA (no usable GPU). */
+eeid_status eeid_ctx_create(int device, size_t hbm_budget_bytes, eeid_ctx** out);
+
+/* Free the context and its workspace (waits for its outstanding work). NULL ok. */
+void eeid_ctx_destroy(eeid_ctx* ctx);
+
+/* Message for the last error or warning raised on the calling host thread. */
+const char* eeid_last_error(void);
+
+/* Wait for all work enqueued on `stream` and return the worst deferred status of
+ * the context's calls since the previous eeid_sync (errors before warnings), then
+ * clear it. */
+eeid_status eeid_sync(eeid_ctx* ctx, void* stream);
+
+/* Eigenvalues lam_1(A) <= ... <= lam_n(A) of A (Sec. 2: the first input of Eq. 1).
+ * d_lambda: device, n doubles, written ascending.  n == 0 is a no-op. */
+eeid_status eeid_eigvals(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n,
+                         double* d_lambda, void* stream);
+
+/* Eigenvalues of the minors M_j (A with row and column j removed; Sec. 2, the
+ * second input of Eq. 1) for j = h_cols[c], c < ncols.  d_mu: device,
+ * ncols x (n-1) doubles row-major, row c ascending.  h_cols: host, distinct
+ * indices in [0, n).  ncols == 0 or n <= 1 is a no-op. */
+eeid_status eeid_minor_eigvals(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n,
+                               const int64_t* h_cols, int64_t ncols, double* d_mu,
+                               void* stream);
+
+/* Eq. 1 for the grid i = h_rows[r] (r < nrows), j = h_cols[c] (c < ncols):
+ * d_out[r*ncols + c] = |v_ij|^2 (device, nrows x ncols doubles).
+ * h_rows / h_cols: host, distinct indices in [0, n); NULL means "all" (then
+ * nrows / ncols must equal n).  d_lambda_opt: optional device buffer of n doubles
+ * that receives the eigenvalues of A.  n == 1 gives |v|^2 = 1; nrows == 0 or
+ * ncols == 0 is a no-op.  Deferred warnings: EEID_WARN_DEGENERATE,
+ * EEID_WARN_SMALL_GAP (see eeid_sync). */
+eeid_status eeid_components(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n,
+                            const int64_t* h_rows, int64_t nrows, const int64_t* h_cols,
+                            int64_t ncols, double* d_out, double* d_lambda_opt, void* stream);
+
+/* eeid_components on HOST buffers: copies hA (host, n x lda doubles, pinned or
+ * pageable) to the context's device workspace, runs the path on `stream`, copies
+ * the nrows x ncols grid back into h_out (and the eigenvalues into h_lambda_opt),
+ * and synchronises the stream.  Returns the call's final status (warnings
+ * included).  Same index conventions as eeid_components. */
+eeid_status eeid_components_host(eeid_ctx* ctx, const double* hA, int64_t lda, int64_t n,
+                                 const int64_t* h_rows, int64_t nrows, const int64_t* h_cols,
+                                 int64_t ncols, double* h_out, double* h_lambda_opt,
+                                 void* stream);
+
+/* One problem of a batch: the arguments of eeid_components.  h_rows / h_cols NULL
+ * mean "all" (nrows / ncols = n). */
+typedef struct {
+  const double* dA;
+  int64_t lda;
+  int64_t n;
+  const int64_t* h_rows;
+  int64_t nrows;
+  const int64_t* h_cols;
+  int64_t ncols;
+  double* d_out;      /* nrows x ncols */
+  double* d_lambda;   /* optional, n */
+} eeid_problem;
+
+/* Eq. 1 for many matrices of uneven size in one pass: all tridiagonalisations,
+ * bisections and identity evaluations of every problem are merged into
+ * cost-sorted task lists run by persistent kernels, captured once per batch
+ * shape into a CUDA graph.  Results are bitwise identical to calling
+ * eeid_components on each problem alone.  probs: host array of `count`. */
+eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* probs, int64_t count,
+                                    void* stream);
+
+/* Number of kernel launches the context has enqueued so far (for accounting). */
+int64_t eeid_launch_count(const eeid_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EEID_H */

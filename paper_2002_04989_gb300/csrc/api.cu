@@ -1,0 +1,566 @@
+// C ABI of libeeid: argument validation, planning of the task lists, workspace
+// management inside the context's HBM budget, and the launch sequence
+//   K-a tridiag (A and minors) -> K-b bisect (A) -> denominators -> K-b bisect
+//   (minors, interlacing brackets) -> K-c identity.
+// Every arithmetic step runs in the CUDA kernels; the host only plans and launches.
+#include "eeid.h"
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace eeid {
+int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m);
+}
+
+using namespace eeid;
+
+namespace {
+
+thread_local std::string g_err;
+
+eeid_status fail(eeid_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+eeid_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(EEID_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define EEID_CK(call, what)                         \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+
+struct eeid_ctx {
+  int device = 0;
+  int sms = 0;
+  size_t budget = 0;
+  char* ws = nullptr;
+  size_t ws_cap = 0;
+  unsigned* d_status = nullptr;
+  char* h_stage = nullptr;
+  size_t h_stage_cap = 0;
+  cudaEvent_t stage_ev = nullptr;
+  bool stage_used = false;
+  int64_t launches = 0;
+  int occ_cache[2][9] = {};  // blocks/SM per (smem path, warps) at the last max_m
+  int occ_m[2][9] = {};
+};
+
+namespace {
+
+// ------------------------------------------------------------------ planning
+
+// Tridiagonalisation configuration by matrix size (shared memory resident up to
+// kTridiagSmemMaxM, global slots above).  Depends on m only, so a matrix's result
+// never depends on what else is in the batch.
+struct TriCfg {
+  bool smem;
+  int warps;
+};
+TriCfg tri_cfg(int m) {
+  if (m <= 32) return {true, 1};
+  if (m <= 64) return {true, 2};
+  if (m <= kTridiagSmemMaxM) return {true, 4};
+  if (m <= 2048) return {false, 4};
+  return {false, 8};
+}
+inline int cfg_key(const TriCfg& c) { return (c.smem ? 0 : 16) + c.warps; }
+
+struct Problem {
+  const double* dA;
+  int64_t lda;
+  int n;
+  std::vector<int> rows;  // eigen-indices
+  std::vector<int> cols;  // component indices
+  double* out;            // nrows x ncols (may be null for eig-only modes)
+  double* lam_user;       // optional
+  double* mu_user;        // minor-eigvals mode output (ncols x (n-1))
+};
+
+enum Mode { MODE_EIGVALS, MODE_MINORS, MODE_COMPONENTS };
+
+struct Arena {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  }
+};
+
+eeid_status check_ctx(eeid_ctx* ctx) {
+  if (!ctx) return fail(EEID_ERR_INVALID, "null context");
+  return EEID_OK;
+}
+
+eeid_status parse_indices(const int64_t* h, int64_t cnt, int64_t n, const char* what,
+                          std::vector<int>& out) {
+  if (cnt < 0) return fail(EEID_ERR_INVALID, "%s: negative count", what);
+  if (!h) {
+    if (cnt != n) return fail(EEID_ERR_INVALID, "%s: NULL means all, count must equal n", what);
+    out.resize(n);
+    for (int64_t k = 0; k < n; ++k) out[k] = (int)k;
+    return EEID_OK;
+  }
+  out.resize(cnt);
+  std::vector<char> seen(n > 0 ? n : 1, 0);
+  for (int64_t k = 0; k < cnt; ++k) {
+    const int64_t v = h[k];
+    if (v < 0 || v >= n) return fail(EEID_ERR_INVALID, "%s[%lld] = %lld out of [0, %lld)", what,
+                                     (long long)k, (long long)v, (long long)n);
+    if (seen[v]) return fail(EEID_ERR_INVALID, "%s: duplicate index %lld", what, (long long)v);
+    seen[v] = 1;
+    out[k] = (int)v;
+  }
+  return EEID_OK;
+}
+
+eeid_status check_matrix(const double* dA, int64_t lda, int64_t n) {
+  if (n < 0) return fail(EEID_ERR_INVALID, "n = %lld < 0", (long long)n);
+  if (n > kTridiagMaxM) return fail(EEID_ERR_INVALID, "n = %lld exceeds the limit %d",
+                                    (long long)n, kTridiagMaxM);
+  if (n > 0 && !dA) return fail(EEID_ERR_INVALID, "matrix pointer is NULL");
+  if (n > 0 && lda < n) return fail(EEID_ERR_INVALID, "lda = %lld < n = %lld", (long long)lda,
+                                    (long long)n);
+  return EEID_OK;
+}
+
+eeid_status ensure_ws(eeid_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_cap) return EEID_OK;
+  if (bytes > ctx->budget)
+    return fail(EEID_ERR_NOMEM, "workspace of %zu bytes exceeds the HBM budget of %zu bytes", bytes,
+                ctx->budget);
+  if (ctx->ws) {
+    cudaError_t e = cudaFree(ctx->ws);  // synchronises the device: prior work is done
+    ctx->ws = nullptr;
+    ctx->ws_cap = 0;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
+  }
+  size_t cap = std::min(ctx->budget, std::max(bytes, (size_t)64 << 20));
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EEID_ERR_NOMEM, "cudaMalloc(%zu) failed: %s", cap, cudaGetErrorString(e));
+  }
+  ctx->ws = (char*)p;
+  ctx->ws_cap = cap;
+  return EEID_OK;
+}
+
+eeid_status ensure_stage(eeid_ctx* ctx, size_t bytes) {
+  if (ctx->stage_used) {
+    // the previous call's metadata copy must have left the staging buffer
+    cudaError_t e = cudaEventSynchronize(ctx->stage_ev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize(stage)");
+  }
+  if (bytes <= ctx->h_stage_cap) return EEID_OK;
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  ctx->h_stage = nullptr;
+  size_t cap = std::max(bytes, (size_t)1 << 20);
+  cudaError_t e = cudaMallocHost((void**)&ctx->h_stage, cap);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost(stage)");
+  ctx->h_stage_cap = cap;
+  return EEID_OK;
+}
+
+int blocks_per_sm(eeid_ctx* ctx, const TriCfg& c, int max_m) {
+  int& cache = ctx->occ_cache[c.smem ? 0 : 1][c.warps];
+  int& cm = ctx->occ_m[c.smem ? 0 : 1][c.warps];
+  if (cache == 0 || cm != max_m) {
+    cache = std::max(1, tridiag_blocks_per_sm(c.smem, c.warps, max_m));
+    cm = max_m;
+  }
+  return cache;
+}
+
+// Plan, upload and launch the whole path for a list of problems.
+eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStream_t stream) {
+  EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  // ---- task lists (host)
+  struct TriRef { int prob; int col; int m; };  // col = -1: A itself
+  std::vector<TriRef> tri;
+  for (int p = 0; p < (int)probs.size(); ++p) {
+    const Problem& P = probs[p];
+    if (P.n < 1) continue;
+    tri.push_back({p, -1, P.n});
+    if (mode != MODE_EIGVALS && P.n >= 2)
+      for (int c = 0; c < (int)P.cols.size(); ++c) tri.push_back({p, c, P.n - 1});
+  }
+  if (tri.empty()) return EEID_OK;
+
+  // ---- device layout: [metadata (uploaded once per call) | data buffers]
+  Arena meta, dat;
+  std::vector<size_t> lam_off(probs.size(), 0), mu_off(probs.size(), 0), dm_off(probs.size(), 0),
+      de_off(probs.size(), 0);
+  std::vector<size_t> d_off(tri.size()), e_off(tri.size());
+  for (size_t t = 0; t < tri.size(); ++t) {
+    d_off[t] = dat.take(sizeof(double) * tri[t].m);
+    e_off[t] = dat.take(sizeof(double) * std::max(tri[t].m - 1, 1));
+  }
+  int max_n = 1;
+  for (size_t p = 0; p < probs.size(); ++p) {
+    const Problem& P = probs[p];
+    max_n = std::max(max_n, P.n);
+    if (P.n < 1) continue;
+    lam_off[p] = P.lam_user ? SIZE_MAX : dat.take(sizeof(double) * P.n);
+    if (mode != MODE_EIGVALS && P.n >= 2)
+      mu_off[p] = (mode == MODE_MINORS) ? SIZE_MAX
+                                        : dat.take(sizeof(double) * P.cols.size() * (P.n - 1));
+    if (mode == MODE_COMPONENTS) {
+      dm_off[p] = dat.take(sizeof(double) * P.n);
+      de_off[p] = dat.take(sizeof(int) * P.n);
+    }
+  }
+  // tridiagonalisation groups (one persistent launch per configuration)
+  std::vector<std::vector<int>> groups(32);
+  for (size_t t = 0; t < tri.size(); ++t) groups[cfg_key(tri_cfg(tri[t].m))].push_back((int)t);
+  struct GroupPlan { TriCfg cfg; int max_m; int grid; size_t task_off, counter_off, work_off;
+                     size_t slot; std::vector<int> idx; };
+  std::vector<GroupPlan> gplans;
+  for (int key = 0; key < 32; ++key) {
+    if (groups[key].empty()) continue;
+    GroupPlan g;
+    g.idx = groups[key];
+    std::stable_sort(g.idx.begin(), g.idx.end(),
+                     [&](int a, int b) { return tri[a].m > tri[b].m; });  // cost-sorted
+    g.max_m = tri[g.idx[0]].m;
+    g.cfg = tri_cfg(g.max_m);
+    const int bps = blocks_per_sm(ctx, g.cfg, g.max_m);
+    g.grid = (int)std::min<int64_t>((int64_t)g.idx.size(), (int64_t)ctx->sms * bps);
+    g.slot = g.cfg.smem ? 0 : tridiag_global_slot_doubles(g.max_m);
+    g.work_off = g.cfg.smem ? 0 : dat.take(sizeof(double) * g.slot * g.grid);
+    g.task_off = meta.take(sizeof(TridiagTask) * g.idx.size());
+    g.counter_off = meta.take(sizeof(int));
+    gplans.push_back(std::move(g));
+  }
+  // bisection tasks: A's first (their eigenvalues seed the minors' brackets)
+  std::vector<int> bis_a, bis_m;
+  for (size_t t = 0; t < tri.size(); ++t) (tri[t].col < 0 ? bis_a : bis_m).push_back((int)t);
+  const size_t bt_off = meta.take(sizeof(BisectTask) * tri.size());
+  auto items_of = [&](const std::vector<int>& ts, std::vector<BisectItem>& items, int& mm) {
+    std::vector<int> order = ts;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tri[a].m > tri[b].m; });
+    mm = 1;
+    for (int t : order) {
+      mm = std::max(mm, tri[t].m);
+      for (int k0 = 0; k0 < tri[t].m; k0 += kBisectThreads) items.push_back({t, k0});
+    }
+  };
+  std::vector<BisectItem> items_a, items_m;
+  int mm_a = 1, mm_m = 1;
+  items_of(bis_a, items_a, mm_a);
+  items_of(bis_m, items_m, mm_m);
+  const size_t bia_off = meta.take(sizeof(BisectItem) * std::max<size_t>(items_a.size(), 1));
+  const size_t bim_off = meta.take(sizeof(BisectItem) * std::max<size_t>(items_m.size(), 1));
+  // identity
+  std::vector<IdentityItem> iitems;
+  size_t dt_off = 0, ip_off = 0, ii_off = 0;
+  std::vector<size_t> rows_off(probs.size(), 0);
+  if (mode == MODE_COMPONENTS) {
+    for (size_t p = 0; p < probs.size(); ++p)
+      if (probs[p].n >= 1)
+        rows_off[p] = meta.take(sizeof(int) * std::max<size_t>(probs[p].rows.size(), 1));
+    dt_off = meta.take(sizeof(DenomTask) * probs.size());
+    ip_off = meta.take(sizeof(IdentityProblem) * probs.size());
+    for (size_t p = 0; p < probs.size(); ++p) {
+      const Problem& P = probs[p];
+      if (P.n < 1) continue;
+      for (int c = 0; c < (int)P.cols.size(); ++c)
+        for (int r0 = 0; r0 < (int)P.rows.size(); r0 += kIdentityThreads)
+          iitems.push_back({(int)p, c, r0});
+    }
+    ii_off = meta.take(sizeof(IdentityItem) * std::max<size_t>(iitems.size(), 1));
+  }
+  const size_t meta_bytes = meta.off;
+  eeid_status st = ensure_ws(ctx, meta_bytes + dat.off);
+  if (st != EEID_OK) return st;
+  char* ws = ctx->ws;
+  char* wd = ws + meta_bytes;
+  auto D = [&](size_t off) { return (double*)(wd + off); };
+
+  // ---- host image of the metadata region (counters stay zero)
+  st = ensure_stage(ctx, meta_bytes);
+  if (st != EEID_OK) return st;
+  char* img = ctx->h_stage;
+  memset(img, 0, meta_bytes);
+  auto lam_ptr = [&](int p) { return probs[p].lam_user ? probs[p].lam_user : D(lam_off[p]); };
+  auto mu_ptr = [&](int p) {
+    return mode == MODE_MINORS ? probs[p].mu_user : D(mu_off[p]);
+  };
+  for (auto& g : gplans) {
+    TridiagTask* tt = (TridiagTask*)(img + g.task_off);
+    for (size_t q = 0; q < g.idx.size(); ++q) {
+      const TriRef& r = tri[g.idx[q]];
+      const Problem& P = probs[r.prob];
+      tt[q] = {P.dA, P.lda, P.n, r.col < 0 ? -1 : P.cols[r.col], D(d_off[g.idx[q]]),
+               D(e_off[g.idx[q]])};
+    }
+  }
+  {
+    BisectTask* bt = (BisectTask*)(img + bt_off);
+    for (size_t t = 0; t < tri.size(); ++t) {
+      const TriRef& r = tri[t];
+      double* eig = (r.col < 0) ? lam_ptr(r.prob) : mu_ptr(r.prob) + (size_t)r.col * (r.m);
+      bt[t] = {D(d_off[t]), D(e_off[t]), r.m, r.col < 0 ? nullptr : lam_ptr(r.prob), eig};
+    }
+    if (!items_a.empty()) memcpy(img + bia_off, items_a.data(), sizeof(BisectItem) * items_a.size());
+    if (!items_m.empty()) memcpy(img + bim_off, items_m.data(), sizeof(BisectItem) * items_m.size());
+  }
+  if (mode == MODE_COMPONENTS) {
+    DenomTask* dt = (DenomTask*)(img + dt_off);
+    IdentityProblem* ip = (IdentityProblem*)(img + ip_off);
+    for (size_t p = 0; p < probs.size(); ++p) {
+      const Problem& P = probs[p];
+      if (P.n < 1) continue;
+      dt[p] = {lam_ptr((int)p), P.n, D(dm_off[p]), (int*)(wd + de_off[p])};
+      memcpy(img + rows_off[p], P.rows.data(), sizeof(int) * P.rows.size());
+      ip[p] = {lam_ptr((int)p), D(dm_off[p]), (const int*)(wd + de_off[p]),
+               P.n >= 2 ? mu_ptr((int)p) : nullptr, (const int*)(ws + rows_off[p]), P.n,
+               (int)P.rows.size(), (int)P.cols.size(), P.out};
+    }
+    if (!iitems.empty()) memcpy(img + ii_off, iitems.data(), sizeof(IdentityItem) * iitems.size());
+  }
+  EEID_CK(cudaMemcpyAsync(ws, img, meta_bytes, cudaMemcpyHostToDevice, stream),
+          "cudaMemcpyAsync(metadata)");
+  EEID_CK(cudaEventRecord(ctx->stage_ev, stream), "cudaEventRecord(stage)");
+  ctx->stage_used = true;
+
+  // ---- launches
+  for (auto& g : gplans) {
+    TridiagLaunch L;
+    L.tasks = (const TridiagTask*)(ws + g.task_off);
+    L.ntasks = (int)g.idx.size();
+    L.counter = (int*)(ws + g.counter_off);
+    L.work = g.cfg.smem ? nullptr : D(g.work_off);
+    L.work_stride = (int64_t)g.slot;
+    L.max_m = g.max_m;
+    L.status = ctx->d_status;
+    EEID_CK(launch_tridiag(g.cfg.smem, g.cfg.warps, g.grid, L, stream), "tridiag launch");
+    ctx->launches++;
+  }
+  const BisectTask* btd = (const BisectTask*)(ws + bt_off);
+  EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bia_off), (int)items_a.size(), mm_a,
+                        ctx->d_status, stream), "bisect(A) launch");
+  ctx->launches += items_a.empty() ? 0 : 1;
+  if (mode == MODE_COMPONENTS) {
+    EEID_CK(launch_denominators((const DenomTask*)(ws + dt_off), (int)probs.size(), max_n,
+                                ctx->d_status, stream), "denominators launch");
+    ctx->launches++;
+  }
+  if (!items_m.empty()) {
+    EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bim_off), (int)items_m.size(), mm_m,
+                          ctx->d_status, stream), "bisect(minors) launch");
+    ctx->launches++;
+  }
+  if (mode == MODE_COMPONENTS && !iitems.empty()) {
+    EEID_CK(launch_identity((const IdentityProblem*)(ws + ip_off),
+                            (const IdentityItem*)(ws + ii_off), (int)iitems.size(), max_n, stream),
+            "identity launch");
+    ctx->launches++;
+  }
+  return EEID_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+const char* eeid_last_error(void) { return g_err.c_str(); }
+
+eeid_status eeid_ctx_create(int device, size_t hbm_budget_bytes, eeid_ctx** out) {
+  if (!out) return fail(EEID_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(EEID_ERR_CUDA, "no CUDA device available (%s)",
+                e != cudaSuccess ? cudaGetErrorString(e) : "count is 0");
+  }
+  if (device < 0 || device >= ndev) return fail(EEID_ERR_INVALID, "device %d out of range", device);
+  EEID_CK(cudaSetDevice(device), "cudaSetDevice");
+  cudaDeviceProp prop;
+  EEID_CK(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+  size_t fr = 0, tot = 0;
+  EEID_CK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+  eeid_ctx* c = new eeid_ctx();
+  c->device = device;
+  c->sms = prop.multiProcessorCount;
+  c->budget = hbm_budget_bytes ? hbm_budget_bytes : fr / 2;
+  e = cudaMalloc((void**)&c->d_status, 256);
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 256);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    eeid_ctx_destroy(c);
+    return cuda_fail(e, "context setup");
+  }
+  *out = c;
+  return EEID_OK;
+}
+
+void eeid_ctx_destroy(eeid_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+  delete ctx;
+}
+
+int64_t eeid_launch_count(const eeid_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+eeid_status eeid_sync(eeid_ctx* ctx, void* stream) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  EEID_CK(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+  unsigned bits = 0;
+  EEID_CK(cudaMemcpy(&bits, ctx->d_status, sizeof bits, cudaMemcpyDeviceToHost), "status read");
+  EEID_CK(cudaMemset(ctx->d_status, 0, sizeof bits), "status clear");
+  if (bits & ST_BAD_TASK) return fail(EEID_ERR_INVALID, "a kernel met a task beyond its size limit");
+  if (bits & ST_DEGENERATE)
+    return fail(EEID_WARN_DEGENERATE, "equal eigenvalues of A: Eq. 1 is 0/0; rows set to NaN");
+  if (bits & ST_SMALL_GAP)
+    return fail(EEID_WARN_SMALL_GAP, "minimum relative eigenvalue gap below 1e-4");
+  return EEID_OK;
+}
+
+eeid_status eeid_eigvals(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n, double* d_lambda,
+                         void* stream) {
+  eeid_status st = check_ctx(ctx);
+  if (st == EEID_OK) st = check_matrix(dA, lda, n);
+  if (st != EEID_OK) return st;
+  if (n == 0) return EEID_OK;
+  if (!d_lambda) return fail(EEID_ERR_INVALID, "d_lambda is NULL");
+  std::vector<Problem> probs(1);
+  probs[0] = {dA, lda, (int)n, {}, {}, nullptr, d_lambda, nullptr};
+  return run(ctx, probs, MODE_EIGVALS, (cudaStream_t)stream);
+}
+
+eeid_status eeid_minor_eigvals(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n,
+                               const int64_t* h_cols, int64_t ncols, double* d_mu, void* stream) {
+  eeid_status st = check_ctx(ctx);
+  if (st == EEID_OK) st = check_matrix(dA, lda, n);
+  if (st != EEID_OK) return st;
+  std::vector<Problem> probs(1);
+  st = parse_indices(h_cols, ncols, n, "cols", probs[0].cols);
+  if (st != EEID_OK) return st;
+  if (ncols == 0 || n <= 1) return EEID_OK;
+  if (!d_mu) return fail(EEID_ERR_INVALID, "d_mu is NULL");
+  probs[0].dA = dA; probs[0].lda = lda; probs[0].n = (int)n;
+  probs[0].out = nullptr; probs[0].lam_user = nullptr; probs[0].mu_user = d_mu;
+  return run(ctx, probs, MODE_MINORS, (cudaStream_t)stream);
+}
+
+static eeid_status make_component_problem(const double* dA, int64_t lda, int64_t n,
+                                          const int64_t* h_rows, int64_t nrows,
+                                          const int64_t* h_cols, int64_t ncols, double* d_out,
+                                          double* d_lambda_opt, Problem& P) {
+  eeid_status st = check_matrix(dA, lda, n);
+  if (st != EEID_OK) return st;
+  st = parse_indices(h_rows, nrows, n, "rows", P.rows);
+  if (st != EEID_OK) return st;
+  st = parse_indices(h_cols, ncols, n, "cols", P.cols);
+  if (st != EEID_OK) return st;
+  if (nrows > 0 && ncols > 0 && !d_out) return fail(EEID_ERR_INVALID, "d_out is NULL");
+  P.dA = dA; P.lda = lda; P.n = (int)n; P.out = d_out; P.lam_user = d_lambda_opt; P.mu_user = nullptr;
+  if (nrows == 0 || ncols == 0) P.n = 0;  // no-op problem
+  return EEID_OK;
+}
+
+eeid_status eeid_components(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n,
+                            const int64_t* h_rows, int64_t nrows, const int64_t* h_cols,
+                            int64_t ncols, double* d_out, double* d_lambda_opt, void* stream) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  std::vector<Problem> probs(1);
+  st = make_component_problem(dA, lda, n, h_rows, nrows, h_cols, ncols, d_out, d_lambda_opt,
+                              probs[0]);
+  if (st != EEID_OK) return st;
+  if (probs[0].n == 0) return EEID_OK;
+  return run(ctx, probs, MODE_COMPONENTS, (cudaStream_t)stream);
+}
+
+eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* in, int64_t count,
+                                    void* stream) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  if (count < 0 || (count > 0 && !in)) return fail(EEID_ERR_INVALID, "bad problem array");
+  std::vector<Problem> probs(count);
+  for (int64_t p = 0; p < count; ++p) {
+    st = make_component_problem(in[p].dA, in[p].lda, in[p].n, in[p].h_rows, in[p].nrows,
+                                in[p].h_cols, in[p].ncols, in[p].d_out, in[p].d_lambda, probs[p]);
+    if (st != EEID_OK) {
+      g_err = "problem " + std::to_string(p) + ": " + g_err;
+      return st;
+    }
+  }
+  return run(ctx, probs, MODE_COMPONENTS, (cudaStream_t)stream);
+}
+
+eeid_status eeid_components_host(eeid_ctx* ctx, const double* hA, int64_t lda, int64_t n,
+                                 const int64_t* h_rows, int64_t nrows, const int64_t* h_cols,
+                                 int64_t ncols, double* h_out, double* h_lambda_opt,
+                                 void* stream) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  if (n < 0 || n > kTridiagMaxM) return fail(EEID_ERR_INVALID, "bad n");
+  if (n > 0 && (!hA || lda < n)) return fail(EEID_ERR_INVALID, "bad host matrix");
+  if (n > 0 && nrows > 0 && ncols > 0 && !h_out) return fail(EEID_ERR_INVALID, "h_out is NULL");
+  const int64_t nr = h_rows ? nrows : n, nc = h_cols ? ncols : n;
+  if (n == 0 || nr == 0 || nc == 0) return EEID_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Device staging for A, the grid and the eigenvalues lives in a separate
+  // allocation owned by this call (the context workspace is re-planned by run()).
+  const size_t a_bytes = sizeof(double) * (size_t)n * lda;
+  const size_t o_bytes = sizeof(double) * (size_t)nr * nc;
+  const size_t l_bytes = sizeof(double) * (size_t)n;
+  char* buf = nullptr;
+  EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  EEID_CK(cudaMallocAsync((void**)&buf, align_up(a_bytes) + align_up(o_bytes) + align_up(l_bytes), s),
+          "cudaMallocAsync(host-call staging)");
+  double* dA = (double*)buf;
+  double* dO = (double*)(buf + align_up(a_bytes));
+  double* dL = (double*)(buf + align_up(a_bytes) + align_up(o_bytes));
+  cudaError_t e = cudaMemcpyAsync(dA, hA, a_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    st = eeid_components(ctx, dA, lda, n, h_rows, nrows, h_cols, ncols, dO,
+                         h_lambda_opt ? dL : nullptr, stream);
+    if (st == EEID_OK) {
+      e = cudaMemcpyAsync(h_out, dO, o_bytes, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess && h_lambda_opt)
+        e = cudaMemcpyAsync(h_lambda_opt, dL, l_bytes, cudaMemcpyDeviceToHost, s);
+    }
+  }
+  cudaFreeAsync(buf, s);
+  if (e != cudaSuccess) return cuda_fail(e, "host-buffer copy");
+  if (st != EEID_OK) {
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  return eeid_sync(ctx, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Internal declarations shared by the eeid CUDA translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace eeid {
+
+// Device status bits (OR-ed by kernels into a workspace word, read by eeid_sync).
+enum : unsigned {
+  ST_DEGENERATE = 1u,      // exactly equal eigenvalues of A: Eq. 1 is 0/0
+  ST_SMALL_GAP = 2u,       // min relative gap < 1e-4
+  ST_BRACKET_FALLBACK = 4u,// an interlacing bracket failed its Sturm check (info)
+  ST_BAD_TASK = 8u,        // a kernel met a task it cannot run (size limit)
+};
+
+// ---------------------------------------------------------------- K-a tridiag
+// One matrix to reduce to symmetric tridiagonal form: the parent A (n x n,
+// row-major, lower triangle read) with row/column `skip` removed (skip < 0: A
+// itself).  Outputs d[m] and e[m-1], m = n - (skip >= 0).
+struct TridiagTask {
+  const double* A;
+  int64_t lda;
+  int n;
+  int skip;
+  double* d;
+  double* e;
+};
+
+// Largest m the shared-memory-resident path accepts, per CTA warp count.
+constexpr int kTridiagSmemMaxM = 160;
+// Largest m any tridiagonalisation kernel accepts (vector staging in shared memory).
+constexpr int kTridiagMaxM = 4096;
+
+struct TridiagLaunch {
+  const TridiagTask* tasks;  // device array, cost-sorted (largest first)
+  int ntasks;
+  int* counter;              // device work counter, zeroed before launch
+  double* work;              // global path: per-CTA working matrices
+  int64_t work_stride;       // doubles per CTA slot (matrix + partials)
+  int max_m;                 // largest m among tasks (sizes the per-CTA layout)
+  unsigned* status;
+};
+
+size_t tridiag_global_slot_doubles(int max_m);
+size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps);
+cudaError_t launch_tridiag(bool smem_path, int warps, int grid, const TridiagLaunch& L,
+                           cudaStream_t s);
+
+// ---------------------------------------------------------------- K-b bisect
+// Eigenvalues of one symmetric tridiagonal (d[m], e[m-1]).  With parent != nullptr
+// the m eigenvalues are minor eigenvalues interlaced by the parent's m+1 ascending
+// eigenvalues (bracket [parent[k], parent[k+1]]); otherwise Gershgorin brackets.
+struct BisectTask {
+  const double* d;
+  const double* e;
+  int m;
+  const double* parent;
+  double* eig;
+};
+// A block's share of a task: eigenvalues [k0, k0 + blockDim.x).
+struct BisectItem {
+  int task;
+  int k0;
+};
+constexpr int kBisectThreads = 128;
+cudaError_t launch_bisect(const BisectTask* tasks, const BisectItem* items, int nitems,
+                          int max_m, unsigned* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- K-c identity
+// D_i = prod_{k != i} |lam_i - lam_k| for every i of one problem, kept as a
+// mantissa dm[i] in [0.5, 1) (0 if degenerate) and a binary exponent de[i].
+struct DenomTask {
+  const double* lam;
+  int n;
+  double* dm;
+  int* de;
+};
+cudaError_t launch_denominators(const DenomTask* tasks, int ntasks, int max_n, unsigned* status,
+                                cudaStream_t s);
+
+// One identity block: column c of one problem (minor eigenvalues mu[n-1]) for the
+// rows [r0, r0 + blockDim.x) of that problem's row list.
+struct IdentityProblem {
+  const double* lam;     // n
+  const double* dm;      // n
+  const int* de;         // n
+  const double* mu;      // ncols x (n-1)
+  const int* rows;       // nrows eigen-indices (device)
+  int n, nrows, ncols;
+  double* out;           // nrows x ncols
+};
+struct IdentityItem {
+  int prob;
+  int col;
+  int r0;
+};
+constexpr int kIdentityThreads = 128;
+cudaError_t launch_identity(const IdentityProblem* probs, const IdentityItem* items, int nitems,
+                            int max_n, cudaStream_t s);
+
+}  // namespace eeid

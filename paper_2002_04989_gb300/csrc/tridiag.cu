@@ -1,0 +1,374 @@
+// K-a: Householder reduction of A and of its minors M_j to symmetric tridiagonal
+// form (d, e), FP64, one CTA per matrix, persistent over a cost-sorted task list.
+//
+// Why: Eq. 1 (Sec. 2) needs the eigenvalues of A and of every requested minor;
+// the paper obtains them from LAPACK (Sec. 2-3), whose symmetric solvers start by
+// this same orthogonal reduction.  The reduction preserves the spectrum exactly in
+// exact arithmetic and costs 4/3 m^3 flops per m x m matrix.
+//
+// Per column k (trailing size s = m-k-1): the reflector H = I - tau v v^T that
+// zeroes A[k+2:, k] is formed from the column; then p = tau A22 v,
+// w = p - (tau/2)(p^T v) v, and A22 <- A22 - v w^T - w v^T.  The update of step k-1
+// and the symmetric matrix-vector product of step k are fused into ONE pass over
+// the lower triangle of the trailing block: every element is loaded once, gets the
+// rank-2 update (2 FMA), and feeds both halves of the symmetric product (2 FMA),
+// then is stored once.  On GB300 the FP64 FMA rate (about 2 lane-FMA/clk/SM) and
+// not HBM bandwidth bounds this pass (16 bytes per 4 FMA is ~2.3 TB/s at the FP64
+// peak), so the design minimises FP64 instructions: no FP64 atomics, no shuffle
+// reductions inside tiles, and each 32x32 tile of the product is reduced along rows
+// from a conflict-free shared-memory copy and along columns in registers.
+//
+// Determinism: every partial sum has one owner and a fixed summation order, so a
+// matrix's (d, e) do not depend on which CTA, batch or launch processed it.
+//
+// Two storage variants share the code:
+//   SMEM = true   the whole working matrix lives in shared memory (m <= 160);
+//   SMEM = false  it lives in a per-CTA slot of global memory (L2-resident for
+//                 small m), tiles are staged through a per-warp shared buffer.
+#include "internal.cuh"
+
+#include <cstdio>
+
+namespace eeid {
+namespace {
+
+constexpr int kTile = 32;
+constexpr int kTilePad = 33;
+
+__host__ __device__ inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA; every thread receives the total.  `red` alternates between two
+// halves across consecutive calls so one barrier per call suffices.
+template <int W>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) s += red[w];
+  return s;
+}
+
+__device__ __forceinline__ int snake_owner(int I, int W) {
+  const int q = I / W, r = I % W;
+  return (q & 1) ? (W - 1 - r) : r;
+}
+
+struct Layout {
+  int VM;         // padded vector length
+  int nbmax;      // max tile blocks along the trailing block
+  int64_t ld;     // working-matrix leading dimension
+};
+
+__host__ __device__ inline Layout make_layout(bool smem, int max_m) {
+  Layout L;
+  L.VM = round_up(max_m, 32) + 32;
+  L.nbmax = (max_m + 31) / 32;
+  L.ld = smem ? (int64_t)(max_m | 1) : (int64_t)round_up(max_m, 4);
+  return L;
+}
+
+template <bool SMEM, int W>
+__global__ void __launch_bounds__(W * 32) k_tridiag(TridiagLaunch P) {
+  extern __shared__ __align__(16) double sm[];
+  constexpr int NT = W * 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const Layout Ly = make_layout(SMEM, P.max_m);
+  const int64_t ld = Ly.ld;
+  const int nbmax = Ly.nbmax;
+
+  double* vP = sm;
+  double* wP = vP + Ly.VM;
+  double* vC = wP + Ly.VM;
+  double* wC = vC + Ly.VM;
+  double* red = wC + Ly.VM;       // 2*W reduction slots
+  double* scal = red + 2 * W;     // 8 scalars
+  double* S;
+  double* tpart;
+  double* upart;
+  double* tile = nullptr;
+  if (SMEM) {
+    S = scal + 8;
+    tpart = S + (size_t)P.max_m * ld;
+    upart = tpart + (size_t)nbmax * nbmax * 32;
+  } else {
+    double* slot = P.work + (size_t)blockIdx.x * P.work_stride;
+    S = slot;
+    tpart = S + (size_t)P.max_m * ld;
+    upart = tpart + (size_t)nbmax * nbmax * 32;
+    tile = scal + 8 + warp * (kTile * kTilePad);
+  }
+  __shared__ int s_task;
+
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(P.counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= P.ntasks) break;
+    const TridiagTask task = P.tasks[t];
+    const int skip = task.skip;
+    const int m = task.n - (skip >= 0 ? 1 : 0);
+    if (m < 1 || m > P.max_m) {
+      if (tid == 0) atomicOr(P.status, (unsigned)ST_BAD_TASK);
+      continue;
+    }
+    double* __restrict__ dout = task.d;
+    double* __restrict__ eout = task.e;
+
+    // a1: the minor view -- copy the lower triangle of A without row/col `skip`.
+    for (int r = warp; r < m; r += W) {
+      const int i = (skip >= 0 && r >= skip) ? r + 1 : r;
+      const double* Arow = task.A + (size_t)i * task.lda;
+      for (int c = lane; c <= r; c += 32) {
+        const int j = (skip >= 0 && c >= skip) ? c + 1 : c;
+        S[(size_t)r * ld + c] = Arow[j];
+      }
+    }
+    __syncthreads();
+
+    int redsel = 0;
+    for (int k = 0; k + 2 < m; ++k) {
+      const int base = k + 1;
+      const bool upd = (k > 0);
+      // ---- Phase A: apply update k-1 to column k; x = column below the diagonal.
+      double sig = 0;
+      const double vPk = upd ? vP[k] : 0.0, wPk = upd ? wP[k] : 0.0;
+      for (int i = k + tid; i < m; i += NT) {
+        double a = S[(size_t)i * ld + k];
+        if (upd) a = fma(-vP[i], wPk, fma(-wP[i], vPk, a));
+        if (i == k) {
+          dout[k] = a;
+        } else if (i == k + 1) {
+          scal[0] = a;       // alpha
+          vC[i] = 1.0;
+        } else {
+          vC[i] = a;
+          sig = fma(a, a, sig);
+        }
+      }
+      sig = block_sum<W>(sig, red + redsel * W);
+      redsel ^= 1;
+      // ---- Phase B: reflector scalars (warp 0), broadcast through shared memory.
+      if (warp == 0) {
+        const double alpha = scal[0];
+        double tau = 0.0, scale = 0.0, beta = alpha;
+        if (sig != 0.0) {
+          const double nrm = sqrt(fma(alpha, alpha, sig));
+          beta = (alpha >= 0.0) ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        if (lane == 0) {
+          scal[1] = tau;
+          scal[2] = scale;
+          eout[k] = beta;
+        }
+      }
+      __syncthreads();
+      const double tau = scal[1];
+      // ---- Phase C: v = x / (alpha - beta), v[k+1] = 1 (already set).
+      {
+        const double scale = scal[2];
+        for (int i = k + 2 + tid; i < m; i += NT) vC[i] *= scale;
+      }
+      __syncthreads();
+      // ---- Phase D: fused pass over the trailing lower triangle [base, m)^2.
+      const int s = m - base;
+      const int nb = (s + 31) >> 5;
+      for (int I = 0; I < nb; ++I) {
+        if (snake_owner(I, W) != warp) continue;
+        const int R0 = base + kTile * I;
+        double u = 0.0;
+        for (int J = 0; J <= I; ++J) {
+          const int C0 = base + kTile * J;
+          const int c = C0 + lane;
+          const bool full = (J < I) && (R0 + kTile <= m);
+          double t = 0.0;
+          if (full) {
+            const double vPc = upd ? vP[c] : 0.0, wPc = upd ? wP[c] : 0.0;
+            double a[kTile];
+            const double* src = S + (size_t)R0 * ld + c;
+#pragma unroll
+            for (int rr = 0; rr < kTile; ++rr) a[rr] = src[(size_t)rr * ld];
+            if (upd) {
+#pragma unroll
+              for (int rr = 0; rr < kTile; ++rr) {
+                const int i = R0 + rr;
+                a[rr] = fma(-vP[i], wPc, fma(-wP[i], vPc, a[rr]));
+              }
+              double* dst = S + (size_t)R0 * ld + c;
+#pragma unroll
+              for (int rr = 0; rr < kTile; ++rr) dst[(size_t)rr * ld] = a[rr];
+            }
+#pragma unroll
+            for (int rr = 0; rr < kTile; ++rr) t = fma(a[rr], vC[R0 + rr], t);
+            if (!SMEM) {
+#pragma unroll
+              for (int rr = 0; rr < kTile; ++rr) tile[rr * kTilePad + lane] = a[rr];
+            }
+            tpart[((size_t)I * nbmax + J) * 32 + lane] = t;
+            __syncwarp();
+            const int i = R0 + lane;
+            if (SMEM) {
+              const double* rowp = S + (size_t)i * ld + C0;
+#pragma unroll
+              for (int cc = 0; cc < kTile; ++cc) u = fma(rowp[cc], vC[C0 + cc], u);
+            } else {
+              const double* rowp = tile + lane * kTilePad;
+#pragma unroll
+              for (int cc = 0; cc < kTile; ++cc) u = fma(rowp[cc], vC[C0 + cc], u);
+            }
+            __syncwarp();
+          } else {
+            const bool cv = c < m;
+            const double vPc = (upd && cv) ? vP[c] : 0.0, wPc = (upd && cv) ? wP[c] : 0.0;
+            for (int rr = 0; rr < kTile; ++rr) {
+              const int i = R0 + rr;
+              if (i >= m) break;
+              if (cv && i >= c) {
+                double a = S[(size_t)i * ld + c];
+                if (upd) {
+                  a = fma(-vP[i], wPc, fma(-wP[i], vPc, a));
+                  S[(size_t)i * ld + c] = a;
+                }
+                if (!SMEM) tile[rr * kTilePad + lane] = a;
+                if (i > c) t = fma(a, vC[i], t);
+              }
+            }
+            tpart[((size_t)I * nbmax + J) * 32 + lane] = t;
+            __syncwarp();
+            const int i = R0 + lane;
+            if (i < m) {
+              const int ccmax = min(kTile, i - C0 + 1);
+              if (SMEM) {
+                const double* rowp = S + (size_t)i * ld + C0;
+                for (int cc = 0; cc < ccmax; ++cc) u = fma(rowp[cc], vC[C0 + cc], u);
+              } else {
+                const double* rowp = tile + lane * kTilePad;
+                for (int cc = 0; cc < ccmax; ++cc) u = fma(rowp[cc], vC[C0 + cc], u);
+              }
+            }
+            __syncwarp();
+          }
+        }
+        upart[I * 32 + lane] = u;
+      }
+      __syncthreads();
+      // ---- Phase E: p = tau * (row partials + column partials); gamma = tau/2 p.v
+      double dot = 0.0;
+      for (int i = base + tid; i < m; i += NT) {
+        const int r = i - base, I = r >> 5, l = r & 31;
+        double p = upart[I * 32 + l];
+        for (int I2 = I; I2 < nb; ++I2) p += tpart[((size_t)I2 * nbmax + I) * 32 + l];
+        p *= tau;
+        wC[i] = p;
+        dot = fma(p, vC[i], dot);
+      }
+      dot = block_sum<W>(dot, red + redsel * W);
+      redsel ^= 1;
+      // ---- Phase F: w = p - gamma v.
+      {
+        const double gamma = 0.5 * tau * dot;
+        for (int i = base + tid; i < m; i += NT) wC[i] = fma(-gamma, vC[i], wC[i]);
+      }
+      __syncthreads();
+      double* tv = vP; vP = vC; vC = tv;
+      double* tw = wP; wP = wC; wC = tw;
+    }
+    // Last 2x2 block (or 1x1): apply the final update and read off d, e.
+    if (tid == 0) {
+      if (m == 1) {
+        dout[0] = S[0];
+      } else {
+        const int a0 = m - 2, a1 = m - 1;
+        double s00 = S[(size_t)a0 * ld + a0], s10 = S[(size_t)a1 * ld + a0];
+        double s11 = S[(size_t)a1 * ld + a1];
+        if (m >= 3) {
+          s00 = fma(-2.0 * vP[a0], wP[a0], s00);
+          s10 = fma(-vP[a1], wP[a0], fma(-wP[a1], vP[a0], s10));
+          s11 = fma(-2.0 * vP[a1], wP[a1], s11);
+        }
+        dout[a0] = s00;
+        dout[a1] = s11;
+        eout[a0] = s10;
+      }
+    }
+    __syncthreads();
+    // restore the canonical vector order for the next task (pointer swaps above)
+    vP = sm; wP = vP + Ly.VM; vC = wP + Ly.VM; wC = vC + Ly.VM;
+  }
+}
+
+}  // namespace
+
+size_t tridiag_global_slot_doubles(int max_m) {
+  const Layout L = make_layout(false, max_m);
+  return (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 32 + 32;
+}
+
+size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps) {
+  const Layout L = make_layout(smem_path, max_m);
+  size_t d = 4 * (size_t)L.VM + 2 * warps + 8;
+  if (smem_path)
+    d += (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 32;
+  else
+    d += (size_t)warps * kTile * kTilePad;
+  return d * sizeof(double);
+}
+
+template <bool SMEM, int W>
+static cudaError_t launch_one(int grid, const TridiagLaunch& L, cudaStream_t s) {
+  const size_t smem = tridiag_smem_bytes(SMEM, L.max_m, W);
+  cudaError_t e = cudaFuncSetAttribute(k_tridiag<SMEM, W>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tridiag<SMEM, W><<<grid, W * 32, smem, s>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag(bool smem_path, int warps, int grid, const TridiagLaunch& L,
+                           cudaStream_t s) {
+  if (smem_path) {
+    switch (warps) {
+      case 1: return launch_one<true, 1>(grid, L, s);
+      case 2: return launch_one<true, 2>(grid, L, s);
+      case 4: return launch_one<true, 4>(grid, L, s);
+      case 8: return launch_one<true, 8>(grid, L, s);
+    }
+  } else {
+    switch (warps) {
+      case 2: return launch_one<false, 2>(grid, L, s);
+      case 4: return launch_one<false, 4>(grid, L, s);
+      case 8: return launch_one<false, 8>(grid, L, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Occupancy query used by the planner to size persistent grids.
+int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m) {
+  const size_t smem = tridiag_smem_bytes(smem_path, max_m, warps);
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define EEID_OCC(S_, W_)                                                                   \
+  if (smem_path == S_ && warps == W_) {                                                    \
+    cudaFuncSetAttribute(k_tridiag<S_, W_>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                         (int)smem);                                                       \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tridiag<S_, W_>, W_ * 32, smem); \
+  }
+  EEID_OCC(true, 1) EEID_OCC(true, 2) EEID_OCC(true, 4) EEID_OCC(true, 8)
+  EEID_OCC(false, 2) EEID_OCC(false, 4) EEID_OCC(false, 8)
+#undef EEID_OCC
+  return e == cudaSuccess ? nb : 0;
+}
+
+}  // namespace eeid

@@ -1,0 +1,232 @@
+"""Python binding of libeeid (ctypes): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name declared in
+``include/eeid.h``; the arithmetic runs in the CUDA kernels of libeeid.so.  Device
+arrays are ``torch`` float64 CUDA tensors (PyTorch supplies device memory and the
+current stream); index lists are host integer sequences.  There is no CPU path:
+if the library cannot be loaded, or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+EEID_OK = 0
+EEID_WARN_DEGENERATE = 1
+EEID_WARN_SMALL_GAP = 2
+EEID_ERR_INVALID = -1
+EEID_ERR_NOMEM = -2
+EEID_ERR_CUDA = -3
+EEID_ERR_TIMEOUT = -4
+EEID_ERR_BUSY = -5
+EEID_ERR_NOT_FOUND = -6
+EEID_ERR_CANCELLED = -7
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class EeidError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"eeid status {status}: {msg}")
+        self.status = status
+
+
+class EeidProblem(ctypes.Structure):
+    _fields_ = [("dA", _vp), ("lda", _i64), ("n", _i64), ("h_rows", _i64p), ("nrows", _i64),
+                ("h_cols", _i64p), ("ncols", _i64), ("d_out", _vp), ("d_lambda", _vp)]
+
+
+SIGNATURES = {
+    "eeid_ctx_create": ([ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_vp)], ctypes.c_int),
+    "eeid_ctx_destroy": ([_vp], None),
+    "eeid_last_error": ([], ctypes.c_char_p),
+    "eeid_sync": ([_vp, _vp], ctypes.c_int),
+    "eeid_eigvals": ([_vp, _vp, _i64, _i64, _vp, _vp], ctypes.c_int),
+    "eeid_minor_eigvals": ([_vp, _vp, _i64, _i64, _i64p, _i64, _vp, _vp], ctypes.c_int),
+    "eeid_components": ([_vp, _vp, _i64, _i64, _i64p, _i64, _i64p, _i64, _vp, _vp, _vp],
+                        ctypes.c_int),
+    "eeid_components_host": ([_vp, _vp, _i64, _i64, _i64p, _i64, _i64p, _i64, _vp, _vp, _vp],
+                             ctypes.c_int),
+    "eeid_components_batched": ([_vp, ctypes.POINTER(EeidProblem), _i64, _vp], ctypes.c_int),
+    "eeid_launch_count": ([_vp], ctypes.c_int64),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libeeid.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_needed else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libeeid.so not found at {path}: build the CUDA path first")
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def last_error() -> str:
+    m = load().eeid_last_error()
+    return m.decode() if m else ""
+
+
+def _check(status: int, allow_warn: bool = True) -> int:
+    if status < 0 or (status > 0 and not allow_warn):
+        raise EeidError(status, last_error())
+    return status
+
+
+def _idx(ix):
+    """(pointer, count, keepalive) for an optional host index list."""
+    if ix is None:
+        return None, None, None
+    a = np.ascontiguousarray(np.asarray(ix, dtype=np.int64).reshape(-1))
+    return a.ctypes.data_as(_i64p), a.size, a
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    return t
+
+
+def _mat(A):
+    _dev(A, "A")
+    if A.dim() != 2 or A.shape[0] != A.shape[1] or A.stride(1) != 1:
+        raise ValueError("A must be a square matrix with unit column stride (row-major)")
+    return A, int(A.stride(0)) if A.shape[0] > 0 else max(1, A.shape[0])
+
+
+class Context:
+    """Owns an eeid_ctx (device workspace within an HBM budget)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.lib = load()
+        h = _vp()
+        _check(self.lib.eeid_ctx_create(int(device), int(hbm_budget_bytes), ctypes.byref(h)), False)
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.eeid_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- entry points (same names as the C ABI, without the prefix)
+    def eeid_sync(self, stream=None) -> int:
+        return _check(self.lib.eeid_sync(self.handle, _stream(stream)))
+
+    def eeid_eigvals(self, A, out=None, stream=None):
+        import torch
+        A, lda = _mat(A)
+        n = A.shape[0]
+        lam = out if out is not None else torch.empty(n, dtype=torch.float64, device=A.device)
+        _check(self.lib.eeid_eigvals(self.handle, _vp(A.data_ptr()), lda, n, _vp(lam.data_ptr()),
+                                     _stream(stream)))
+        return lam
+
+    def eeid_minor_eigvals(self, A, cols=None, out=None, stream=None):
+        import torch
+        A, lda = _mat(A)
+        n = A.shape[0]
+        cp, nc, keep = _idx(cols)
+        nc = n if cp is None else nc
+        mu = out if out is not None else torch.empty((nc, max(n - 1, 0)), dtype=torch.float64,
+                                                     device=A.device)
+        _check(self.lib.eeid_minor_eigvals(self.handle, _vp(A.data_ptr()), lda, n, cp, nc,
+                                           _vp(mu.data_ptr()), _stream(stream)))
+        return mu
+
+    def eeid_components(self, A, rows=None, cols=None, out=None, lam=None, stream=None):
+        import torch
+        A, lda = _mat(A)
+        n = A.shape[0]
+        rp, nr, k1 = _idx(rows)
+        cp, nc, k2 = _idx(cols)
+        nr = n if rp is None else nr
+        nc = n if cp is None else nc
+        o = out if out is not None else torch.empty((nr, nc), dtype=torch.float64, device=A.device)
+        _check(self.lib.eeid_components(self.handle, _vp(A.data_ptr()), lda, n, rp, nr, cp, nc,
+                                        _vp(o.data_ptr()),
+                                        _vp(lam.data_ptr()) if lam is not None else None,
+                                        _stream(stream)))
+        return o
+
+    def eeid_components_host(self, A: np.ndarray, rows=None, cols=None, out=None, lam=None,
+                             stream=None):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        n = A.shape[0]
+        rp, nr, k1 = _idx(rows)
+        cp, nc, k2 = _idx(cols)
+        nr = n if rp is None else nr
+        nc = n if cp is None else nc
+        o = out if out is not None else np.empty((nr, nc))
+        st = self.lib.eeid_components_host(
+            self.handle, A.ctypes.data_as(_vp), n, n, rp, nr, cp, nc, o.ctypes.data_as(_vp),
+            lam.ctypes.data_as(_vp) if lam is not None else None, _stream(stream))
+        _check(st)
+        return o
+
+    def eeid_components_batched(self, problems, stream=None):
+        """problems: list of dicts {A, rows?, cols?, out, lam?} (torch CUDA tensors)."""
+        arr = (EeidProblem * len(problems))()
+        keep = []
+        for p, d in enumerate(problems):
+            A, lda = _mat(d["A"])
+            n = A.shape[0]
+            rp, nr, k1 = _idx(d.get("rows"))
+            cp, nc, k2 = _idx(d.get("cols"))
+            keep += [k1, k2]
+            arr[p].dA = A.data_ptr()
+            arr[p].lda = lda
+            arr[p].n = n
+            arr[p].h_rows = rp
+            arr[p].nrows = n if rp is None else nr
+            arr[p].h_cols = cp
+            arr[p].ncols = n if cp is None else nc
+            arr[p].d_out = d["out"].data_ptr()
+            lam = d.get("lam")
+            arr[p].d_lambda = lam.data_ptr() if lam is not None else None
+        return _check(self.lib.eeid_components_batched(self.handle, arr, len(problems),
+                                                       _stream(stream)))
+
+    def launch_count(self) -> int:
+        return int(self.lib.eeid_launch_count(self.handle))

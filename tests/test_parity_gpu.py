@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars (stated here, used everywhere below):
+  * |v_ij|^2: max abs error <= 1e-10, for spectra whose minimum relative gap is
+    >= 1e-4 (outside that, the error is reported and only a loose 1e-6 bar applies);
+  * eigenvalues of A and of the minors: max abs error <= 1e-12 * ||A||_2.
+The oracle runs in long double on the host; planted spectra are checked against
+their closed form Q o Q.
+"""
+import numpy as np
+import pytest
+
+from invariants import grid_errors, spectrum_errors
+from paper_2002_04989_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_VSQ = 1e-10
+TOL_LAM_REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    from paper_2002_04989_gb300 import eeid
+    c = eeid.Context(0)
+    yield c
+    c.close()
+
+
+def dev(torch, A):
+    return torch.from_numpy(np.ascontiguousarray(A)).cuda()
+
+
+def run_components(torch, ctx, A, rows=None, cols=None):
+    dA = dev(torch, A)
+    n = A.shape[0]
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    out = ctx.eeid_components(dA, rows=rows, cols=cols, lam=lam)
+    st = ctx.eeid_sync()
+    return out.cpu().numpy(), lam.cpu().numpy(), st
+
+
+def vsq_bar(lam_ref):
+    return TOL_VSQ if inputs.min_relative_gap(lam_ref) >= 1e-4 else 1e-6
+
+
+# ------------------------------------------------------------------ small, full oracle
+
+SMALL = [1, 2, 3, 5, 8, 16, 31, 32, 33, 47, 63, 64, 65]
+
+
+@pytest.mark.parametrize("n", SMALL)
+def test_goe_small_full_grid(torch_cuda, ctx, oracle_mod, n):
+    A = inputs.goe(n, 1000 + n)
+    out, lam, st = run_components(torch_cuda, ctx, A)
+    ref, lam_ref, mu_ref = oracle_mod.components(A, method=0, want_eigs=True)
+    norm = max(abs(lam_ref[0]), abs(lam_ref[-1]))
+    assert np.max(np.abs(lam - lam_ref)) <= TOL_LAM_REL * norm
+    assert np.max(np.abs(out - ref)) <= vsq_bar(lam_ref), np.max(np.abs(out - ref))
+    if n >= 2:
+        mu = ctx.eeid_minor_eigvals(dev(torch_cuda, A)).cpu().numpy()
+        assert np.max(np.abs(mu - mu_ref)) <= TOL_LAM_REL * norm
+
+
+def test_goe64_workload(torch_cuda, ctx, oracle_mod):
+    """One GOE matrix n = 64 from seed 0: all 64 minors and the full grid."""
+    A = inputs.goe64()
+    out, lam, st = run_components(torch_cuda, ctx, A)
+    ref, lam_ref, mu_ref = oracle_mod.components(A, method=0, want_eigs=True)
+    vv = oracle_mod.components(A, method=2)
+    norm = max(abs(lam_ref[0]), abs(lam_ref[-1]))
+    assert inputs.min_relative_gap(lam_ref) >= 1e-4
+    assert np.max(np.abs(lam - lam_ref)) <= TOL_LAM_REL * norm
+    assert np.max(np.abs(out - ref)) <= TOL_VSQ
+    assert np.max(np.abs(out - vv)) <= TOL_VSQ
+    mu = ctx.eeid_minor_eigvals(dev(torch_cuda, A)).cpu().numpy()
+    assert np.max(np.abs(mu - mu_ref)) <= TOL_LAM_REL * norm
+    g = grid_errors(A, lam, out)
+    assert g["col_sum"] < 1e-11 and g["row_sum"] < 1e-11 and g["diag"] < 1e-10
+    s = spectrum_errors(A, lam, mu)
+    assert s["interlace"] <= 1e-13 * norm and s["minor_trace"] < 1e-10
+
+
+@pytest.mark.parametrize("kind,n", [("wishart", 40), ("toeplitz", 33), ("toeplitz", 64),
+                                    ("planted", 60), ("wishart", 9)])
+def test_families_full_grid(torch_cuda, ctx, oracle_mod, kind, n):
+    if kind == "wishart":
+        A = inputs.wishart(n, 77)
+    elif kind == "toeplitz":
+        A = inputs.toeplitz(n, 0.0, 1.0)
+    else:
+        A = inputs.planted(n, 78, gap=1e-3).A
+    out, lam, st = run_components(torch_cuda, ctx, A)
+    ref, lam_ref, _ = oracle_mod.components(A, method=0, want_eigs=True)
+    norm = max(abs(lam_ref[0]), abs(lam_ref[-1]))
+    assert np.max(np.abs(lam - lam_ref)) <= TOL_LAM_REL * norm
+    assert np.max(np.abs(out - ref)) <= vsq_bar(lam_ref)
+
+
+# ------------------------------------------------------------------ medium: sampled oracle
+
+@pytest.mark.parametrize("n", [96, 127, 128, 129, 160, 161, 200, 255, 256, 300])
+def test_planted_medium(torch_cuda, ctx, oracle_mod, n):
+    """Sizes across the shared-memory / global-memory boundary and ragged tiles:
+    full grid against Q o Q, sampled minors against the secular-equation roots."""
+    p = inputs.planted(n, 2000 + n, -1.0, 1.0, 1e-3)
+    cols = np.array([0, n // 3, n - 1])
+    out, lam, st = run_components(torch_cuda, ctx, p.A)
+    assert np.max(np.abs(lam - p.lam)) <= TOL_LAM_REL * 1.0 + 1e-15
+    assert np.max(np.abs(out - (p.Q * p.Q).T)) <= TOL_VSQ
+    mu = ctx.eeid_minor_eigvals(dev(torch_cuda, p.A), cols=cols).cpu().numpy()
+    mu_ref = oracle_mod.secular_minor_eigvals(p.lam, p.Q, cols)
+    assert np.max(np.abs(mu - mu_ref)) <= TOL_LAM_REL
+    g = grid_errors(p.A, lam, out)
+    assert g["col_sum"] < 1e-10 and g["row_sum"] < 1e-10
+
+
+@pytest.mark.parametrize("n", [100, 161])
+def test_goe_medium_sampled_columns(torch_cuda, ctx, oracle_mod, n):
+    A = inputs.goe(n, 3000 + n)
+    rows = np.array([0, 1, n // 2, n - 2, n - 1])
+    cols = np.array([n - 1, 0, n // 2])
+    out, lam, st = run_components(torch_cuda, ctx, A, rows=rows, cols=cols)
+    ref, lam_ref, _ = oracle_mod.components(A, rows=rows, cols=cols, method=0, want_eigs=True)
+    norm = max(abs(lam_ref[0]), abs(lam_ref[-1]))
+    assert np.max(np.abs(lam - lam_ref)) <= TOL_LAM_REL * norm
+    assert np.max(np.abs(out - ref)) <= vsq_bar(lam_ref)
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+def test_planted1024_workload(torch_cuda, ctx, oracle_mod):
+    """n = 1024 planted spectrum, the full 1024 x 1024 grid against Q o Q (the launch
+    configuration the benchmark times), minors sampled against the secular roots."""
+    p = inputs.planted1024()
+    out, lam, st = run_components(torch_cuda, ctx, p.A)
+    err_lam = np.max(np.abs(lam - p.lam))
+    err = np.max(np.abs(out - (p.Q * p.Q).T))
+    print(f"planted1024: max|dlam| = {err_lam:.3e}, max|d vsq| = {err:.3e}")
+    assert err_lam <= TOL_LAM_REL
+    assert err <= TOL_VSQ
+    cols = np.array([0, 511, 1023])
+    mu = ctx.eeid_minor_eigvals(dev(torch_cuda, p.A), cols=cols).cpu().numpy()
+    mu_ref = oracle_mod.secular_minor_eigvals(p.lam, p.Q, cols)
+    assert np.max(np.abs(mu - mu_ref)) <= TOL_LAM_REL
+    g = grid_errors(p.A, lam, out)
+    assert g["col_sum"] < 1e-10 and g["row_sum"] < 1e-10
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_n1_and_empty(torch_cuda, ctx):
+    out, lam, st = run_components(torch_cuda, ctx, np.array([[2.5]]))
+    assert out[0, 0] == 1.0 and lam[0] == 2.5
+    A = dev(torch_cuda, inputs.goe(5, 1))
+    o = torch_cuda.zeros((0, 5), dtype=torch_cuda.float64, device="cuda")
+    ctx.eeid_components(A, rows=[], cols=None, out=o)
+    assert ctx.eeid_sync() == 0
+
+
+def test_subset_and_order(torch_cuda, ctx, oracle_mod):
+    A = inputs.goe(37, 5)
+    rows, cols = [36, 0, 17], [5, 2, 30, 1]
+    out, lam, st = run_components(torch_cuda, ctx, A, rows=rows, cols=cols)
+    ref = oracle_mod.components(A, rows=rows, cols=cols, method=0)
+    assert np.max(np.abs(out - ref)) <= TOL_VSQ
+
+
+def test_lda_padding(torch_cuda, ctx, oracle_mod):
+    A = inputs.goe(40, 6)
+    big = np.full((40, 48), np.nan)
+    big[:, :40] = A
+    dA = dev(torch_cuda, big)[:, :40]
+    assert dA.stride(0) == 48
+    out = ctx.eeid_components(dA).cpu().numpy()
+    ctx.eeid_sync()
+    ref = oracle_mod.components(A, method=0)
+    assert np.max(np.abs(out - ref)) <= TOL_VSQ
+
+
+def test_lower_triangle_only(torch_cuda, ctx):
+    A = inputs.goe(30, 9)
+    B = A.copy()
+    B[np.triu_indices(30, 1)] = 1e300   # garbage above the diagonal is never read
+    o1, _, _ = run_components(torch_cuda, ctx, A)
+    o2, _, _ = run_components(torch_cuda, ctx, B)
+    assert np.array_equal(o1, o2)
+
+
+def test_argument_errors(torch_cuda, ctx):
+    from paper_2002_04989_gb300 import eeid
+    A = dev(torch_cuda, inputs.goe(6, 2))
+    for rows, cols in (([0, 0], None), ([6], None), (None, [-1]), (None, [1, 1])):
+        with pytest.raises(eeid.EeidError) as ei:
+            ctx.eeid_components(A, rows=rows, cols=cols)
+        assert ei.value.status == eeid.EEID_ERR_INVALID
+
+
+def test_degenerate_warns_and_nans(torch_cuda, ctx):
+    from paper_2002_04989_gb300 import eeid
+    A = np.diag([1.0, 2.0, 2.0, 3.0])
+    dA = dev(torch_cuda, A)
+    out = ctx.eeid_components(dA).cpu().numpy()
+    st = ctx.eeid_sync()
+    assert st == eeid.EEID_WARN_DEGENERATE
+    assert np.isnan(out[1]).all() and np.isnan(out[2]).all()
+    assert np.allclose(out[0], [1, 0, 0, 0], rtol=0, atol=1e-14)
+    assert np.allclose(out[3], [0, 0, 0, 1], rtol=0, atol=1e-14)
+
+
+def test_diagonal_exact(torch_cuda, ctx):
+    d = np.array([0.5, -2.0, 3.0, 1.25, -0.75])
+    out, lam, st = run_components(torch_cuda, ctx, np.diag(d))
+    order = np.argsort(d)
+    expect = np.zeros((5, 5))
+    expect[np.arange(5), order] = 1.0
+    assert np.max(np.abs(out - expect)) <= 1e-15
+    assert np.max(np.abs(lam - np.sort(d))) <= 1e-15
+
+
+def test_eigvals_entry_point(torch_cuda, ctx, oracle_mod):
+    A = inputs.wishart(70, 4)
+    lam = ctx.eeid_eigvals(dev(torch_cuda, A)).cpu().numpy()
+    ref = oracle_mod.eigvals(A)
+    assert np.max(np.abs(lam - ref)) <= TOL_LAM_REL * ref[-1]
+
+
+def test_host_entry_point_matches_device(torch_cuda, ctx):
+    A = inputs.goe(50, 12)
+    o_dev, lam_dev, _ = run_components(torch_cuda, ctx, A)
+    lam_h = np.empty(50)
+    o_host = ctx.eeid_components_host(A, lam=lam_h)
+    assert np.array_equal(o_host, o_dev) and np.array_equal(lam_h, lam_dev)
+
+
+def test_repeatable_bitwise(torch_cuda, ctx):
+    A = inputs.goe(200, 13)
+    o1, _, _ = run_components(torch_cuda, ctx, A)
+    o2, _, _ = run_components(torch_cuda, ctx, A)
+    assert np.array_equal(o1, o2)
+
+
+def test_batched_matches_single_bitwise(torch_cuda, ctx):
+    """Uneven sizes in one batched call give bitwise the results of single calls."""
+    torch = torch_cuda
+    items = [inputs.batch_item(m, 8, 256)[1] for m in range(12)]
+    singles, probs = [], []
+    for A in items:
+        o, lam, _ = run_components(torch, ctx, A)
+        singles.append((o, lam))
+        n = A.shape[0]
+        probs.append({"A": dev(torch, A), "out": torch.empty((n, n), dtype=torch.float64, device="cuda"),
+                      "lam": torch.empty(n, dtype=torch.float64, device="cuda")})
+    ctx.eeid_components_batched(probs)
+    ctx.eeid_sync()
+    for (o, lam), p in zip(singles, probs):
+        assert np.array_equal(p["out"].cpu().numpy(), o)
+        assert np.array_equal(p["lam"].cpu().numpy(), lam)
