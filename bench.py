@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the eigenvector-eigenvalue identity path on GB300.
+
+Default workload: one FP64 matrix n = 1024 with a planted spectrum (Q from a
+Householder QR of a seeded Gaussian matrix, eigenvalues uniform on [-1, 1] with
+minimum gap 1e-4), the full 1024 x 1024 grid |v_ij|^2.  One step = one call of
+eeid_components over that grid (all five phases: Householder reduction of A and
+its 1024 minors, bisection of A, denominators, bisection of the minors, Eq. 1).
+Metric: |v_ij|^2 components per second (higher is better).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+For N > 1 launch under torchrun: each rank runs its own replica of the workload
+(weak scaling, no data-path collective); rank 0 prints one JSON line with the
+aggregate over ranks and the max time over ranks.  --impl reference times the CPU
+oracle (long double, host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "|v_ij|^2 components/s at <=1e-10 err"
+UNIT = "components/s"
+WORKLOAD = ("planted1024: one FP64 n=1024 planted-spectrum matrix (lam uniform on [-1,1], "
+            "min gap 1e-4), full 1024x1024 |v_ij|^2 grid")
+N = 1024
+
+# FP64 peak of one GB300 derived from its unit counts and clock: 152 SMs x 2 FP64
+# FMA lanes/clk/SM (4 flop/clk/SM; 1.25 TFLOP/s nominal) x 2.07 GHz max SM clock.
+FP64_PEAK_GFLOPS = 152 * 4 * 2.07
+# Algorithmic work of the dominant kernel (Householder tridiagonalisation, 4/3 m^3
+# flops per m x m matrix) for one step: A (m = n) plus n minors (m = n - 1).
+TRIDIAG_FLOPS = 4.0 / 3.0 * (N ** 3 + N * (N - 1) ** 3)
+
+# DRAM traffic of one k_tridiag launch from an ncu capture (profiles/), valid only
+# while the kernel source is unchanged (sha256 of csrc/tridiag.cu at capture time).
+TRIDIAG_TRAFFIC = {"bytes_per_launch": None, "source_sha256": None}
+
+
+def src_sha(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world: int, backend: str):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float, device=None) -> float:
+    """Max of a float over all ranks (timing aggregation, not a data-path collective)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(units_per_rank_per_step: float, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: units all ranks processed / max time over ranks."""
+    return units_per_rank_per_step * world * steps / (max_ms / 1e3)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def oracle_sample(planted, target_s: float = 15.0):
+    """Time the CPU oracle on a bounded sample of the workload: the components of
+    whole columns j, i.e. the minor eigenvalues of M_j (roots of the secular equation
+    from the known (lam, Q), long double) followed by Eq. 1 in long double for all i.
+    Returns (components/s, columns, seconds, cores)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    lam, Q = planted.lam, planted.Q
+    # one column first to size the sample, then as many as fit in the target
+    t0 = time.perf_counter()
+    mu = oracle.secular_minor_eigvals(lam, Q, [0])
+    oracle.identity(lam, mu)
+    one = time.perf_counter() - t0
+    ncols = int(max(1, min(N - 1, (target_s / max(one, 1e-3)) * cores)))
+    ncols = max(cores, (ncols // cores) * cores) if ncols >= cores else ncols
+    cols = np.arange(1, 1 + min(ncols, N - 1))
+    t0 = time.perf_counter()
+    mu = oracle.secular_minor_eigvals(lam, Q, cols)
+    oracle.identity(lam, mu)
+    dt = time.perf_counter() - t0
+    return N * cols.size / dt, int(cols.size), dt, cores
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    from paper_2002_04989_gb300 import inputs
+    p = inputs.planted1024()
+    vals, secs, cols = [], [], 0
+    for step in range(args.warmup + args.steps):
+        v, c, dt, cores = oracle_sample(p, target_s=min(10.0, 100.0 / max(1, args.steps)))
+        if step >= args.warmup:
+            vals.append(v)
+            secs.append(dt)
+            cols = c
+    value = statistics.mean(vals)
+    sample = (f"{cols} columns j of the n=1024 planted matrix per step: minor eigenvalues by "
+              f"secular-equation bisection from the planted (lam, Q), then Eq. 1, long double, "
+              f"OpenMP over columns")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2002_04989_gb300 import eeid, inputs
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    p = inputs.planted1024()
+    A = torch.from_numpy(p.A).to(dev)
+    out = torch.empty((N, N), dtype=torch.float64, device=dev)
+    lam = torch.empty(N, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    ctx = eeid.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ctx.eeid_components(A, out=out, lam=lam, stream=stream)
+        flush.fill_(step.counter & 0xff)   # evict L2 between steps
+        step.counter += 1
+    step.counter = 0
+
+    for _ in range(args.warmup):
+        step()
+    st = ctx.eeid_sync(stream)
+    # accuracy of the timed configuration against the planted closed form
+    err = float(np.max(np.abs(out.cpu().numpy() - (p.Q * p.Q).T)))
+
+    ctx.eeid_set_timing(True)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = ctx.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tri_ms, phases = [], []
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        ph = ctx.eeid_phase_times()      # waits for this step's phase events only
+        phases.append(ph)
+        tri_ms.append(ph["tridiag"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    max_ms = max_over_ranks(dist, ms, dev)
+    value = aggregate_value(N * N, world, args.steps, max_ms)
+    ctx.eeid_set_timing(False)
+
+    # ---- end to end: host buffers through the public C ABI (copies in the region)
+    hA = torch.from_numpy(p.A).pin_memory().numpy()
+    hout = torch.empty((N, N), dtype=torch.float64).pin_memory().numpy()
+    hlam = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    ctx.eeid_components_host(hA, out=hout, lam=hlam)
+    barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.eeid_components_host(hA, out=hout, lam=hlam)
+        flush.fill_(1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier(dist)
+    e2e_max = max_over_ranks(dist, e2e_s * 1e3, dev)
+    e2e_value = aggregate_value(N * N, world, args.steps, e2e_max)
+
+    # ---- roofline of the dominant kernel (tridiagonalisation), FP64 ALU bound
+    tri_avg = statistics.mean(tri_ms)
+    achieved = TRIDIAG_FLOPS / (tri_avg / 1e3) / 1e12
+    peak = FP64_PEAK_GFLOPS / 1e3
+    sha = src_sha(os.path.join(ROOT, "paper_2002_04989_gb300", "csrc", "tridiag.cu"))
+    traffic = (TRIDIAG_TRAFFIC["bytes_per_launch"]
+               if TRIDIAG_TRAFFIC["source_sha256"] == sha else None)
+    phase_avg = {k: round(statistics.mean(ph[k] for ph in phases), 3) for k in phases[0]}
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, c, dt, cores = oracle_sample(p)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"{c} columns j of the same matrix ({c * N} components, {dt:.1f} s): "
+                          f"minor eigenvalues by secular-equation bisection from the planted "
+                          f"(lam, Q), then Eq. 1, long double, OpenMP over columns")}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded planted spectrum; no dataset)",
+        "config": {"workload": WORKLOAD, "n": N, "components_per_step_per_gpu": N * N,
+                   "l2": "flushed between steps (256 MiB write, inside the timed region)",
+                   "parallelism": f"replicas x{world} (weak scaling, no collective)"},
+        "roofline": {"bound": "alu", "kernel": "k_tridiag (FP64 Householder, A + 1024 minors)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz "
+                                    "(recipe: 1.25 TFLOP/s nominal)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N * N,
+                "d2h_bytes_per_step": 8 * N * N + 8 * N},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "phases_ms": phase_avg,
+        "max_abs_err_vs_QoQ": err,
+        "status": st,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle timing (profiling runs)")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)   # timing rule: at least 3 untimed warm-up steps
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -140,6 +140,25 @@ eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* probs, in
 /* Number of kernel launches the context has enqueued so far (for accounting). */
 int64_t eeid_launch_count(const eeid_ctx* ctx);
 
+/* Phases of one call, in launch order, for eeid_phase_times. */
+enum {
+  EEID_PHASE_TRIDIAG = 0,       /* Householder reduction of A and of the minors */
+  EEID_PHASE_BISECT_A = 1,      /* eigenvalues of A */
+  EEID_PHASE_DENOMINATORS = 2,  /* prod_{k != i} (lam_i - lam_k), once per i */
+  EEID_PHASE_BISECT_MINORS = 3, /* eigenvalues of the minors */
+  EEID_PHASE_IDENTITY = 4,      /* Eq. 1 for the requested grid */
+  EEID_NUM_PHASES = 5
+};
+
+/* Enable (1) or disable (0) per-phase device timing: each later call records CUDA
+ * events on its stream around its phases (a small cost per launch). */
+eeid_status eeid_set_timing(eeid_ctx* ctx, int enable);
+
+/* Wait for the last timed call's events and write its per-phase device durations
+ * in milliseconds into ms[0 .. min(cap, EEID_NUM_PHASES)) (0 for phases that call
+ * did not run).  Returns the number of values written, or a negative status. */
+int eeid_phase_times(eeid_ctx* ctx, double* ms, int cap);
+
 #ifdef __cplusplus
 }
 #endif

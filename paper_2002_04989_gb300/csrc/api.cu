@@ -62,6 +62,9 @@ struct eeid_ctx {
   int64_t launches = 0;
   int occ_cache[2][9] = {};  // blocks/SM per (smem path, warps) at the last max_m
   int occ_m[2][9] = {};
+  bool timing = false;
+  cudaEvent_t ev[EEID_NUM_PHASES][2] = {};
+  bool ran[EEID_NUM_PHASES] = {};
 };
 
 namespace {
@@ -344,7 +347,14 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   EEID_CK(cudaEventRecord(ctx->stage_ev, stream), "cudaEventRecord(stage)");
   ctx->stage_used = true;
 
-  // ---- launches
+  // ---- launches (optionally bracketed by per-phase events)
+  for (int ph = 0; ph < EEID_NUM_PHASES; ++ph) ctx->ran[ph] = false;
+  auto mark = [&](int ph, int which) -> cudaError_t {
+    if (!ctx->timing) return cudaSuccess;
+    if (which == 1) ctx->ran[ph] = true;
+    return cudaEventRecord(ctx->ev[ph][which], stream);
+  };
+  EEID_CK(mark(EEID_PHASE_TRIDIAG, 0), "event");
   for (auto& g : gplans) {
     TridiagLaunch L;
     L.tasks = (const TridiagTask*)(ws + g.task_off);
@@ -357,25 +367,36 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     EEID_CK(launch_tridiag(g.cfg.smem, g.cfg.warps, g.grid, L, stream), "tridiag launch");
     ctx->launches++;
   }
+  EEID_CK(mark(EEID_PHASE_TRIDIAG, 1), "event");
   const BisectTask* btd = (const BisectTask*)(ws + bt_off);
-  EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bia_off), (int)items_a.size(), mm_a,
-                        ctx->d_status, stream), "bisect(A) launch");
-  ctx->launches += items_a.empty() ? 0 : 1;
+  if (!items_a.empty()) {
+    EEID_CK(mark(EEID_PHASE_BISECT_A, 0), "event");
+    EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bia_off), (int)items_a.size(), mm_a,
+                          ctx->d_status, stream), "bisect(A) launch");
+    ctx->launches++;
+    EEID_CK(mark(EEID_PHASE_BISECT_A, 1), "event");
+  }
   if (mode == MODE_COMPONENTS) {
+    EEID_CK(mark(EEID_PHASE_DENOMINATORS, 0), "event");
     EEID_CK(launch_denominators((const DenomTask*)(ws + dt_off), (int)probs.size(), max_n,
                                 ctx->d_status, stream), "denominators launch");
     ctx->launches++;
+    EEID_CK(mark(EEID_PHASE_DENOMINATORS, 1), "event");
   }
   if (!items_m.empty()) {
+    EEID_CK(mark(EEID_PHASE_BISECT_MINORS, 0), "event");
     EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bim_off), (int)items_m.size(), mm_m,
                           ctx->d_status, stream), "bisect(minors) launch");
     ctx->launches++;
+    EEID_CK(mark(EEID_PHASE_BISECT_MINORS, 1), "event");
   }
   if (mode == MODE_COMPONENTS && !iitems.empty()) {
+    EEID_CK(mark(EEID_PHASE_IDENTITY, 0), "event");
     EEID_CK(launch_identity((const IdentityProblem*)(ws + ip_off),
                             (const IdentityItem*)(ws + ii_off), (int)iitems.size(), max_n, stream),
             "identity launch");
     ctx->launches++;
+    EEID_CK(mark(EEID_PHASE_IDENTITY, 1), "event");
   }
   return EEID_OK;
 }
@@ -426,10 +447,43 @@ void eeid_ctx_destroy(eeid_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+  for (int p = 0; p < EEID_NUM_PHASES; ++p)
+    for (int w = 0; w < 2; ++w)
+      if (ctx->ev[p][w]) cudaEventDestroy(ctx->ev[p][w]);
   delete ctx;
 }
 
 int64_t eeid_launch_count(const eeid_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+eeid_status eeid_set_timing(eeid_ctx* ctx, int enable) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (enable && !ctx->ev[0][0]) {
+    for (int p = 0; p < EEID_NUM_PHASES; ++p)
+      for (int w = 0; w < 2; ++w) EEID_CK(cudaEventCreate(&ctx->ev[p][w]), "cudaEventCreate");
+  }
+  ctx->timing = enable != 0;
+  return EEID_OK;
+}
+
+int eeid_phase_times(eeid_ctx* ctx, double* ms, int cap) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  if (!ms || cap < 0) return fail(EEID_ERR_INVALID, "bad output array");
+  if (!ctx->ev[0][0]) return fail(EEID_ERR_INVALID, "timing was never enabled");
+  EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const int n = cap < EEID_NUM_PHASES ? cap : EEID_NUM_PHASES;
+  for (int p = 0; p < n; ++p) {
+    ms[p] = 0.0;
+    if (!ctx->ran[p]) continue;
+    EEID_CK(cudaEventSynchronize(ctx->ev[p][1]), "cudaEventSynchronize");
+    float t = 0.f;
+    EEID_CK(cudaEventElapsedTime(&t, ctx->ev[p][0], ctx->ev[p][1]), "cudaEventElapsedTime");
+    ms[p] = t;
+  }
+  return n;
+}
 
 eeid_status eeid_sync(eeid_ctx* ctx, void* stream) {
   eeid_status st = check_ctx(ctx);

@@ -91,6 +91,10 @@ k_bisect(const BisectTask* __restrict__ tasks, const BisectItem* __restrict__ it
   const BisectItem it = items[blockIdx.x];
   const BisectTask T = tasks[it.task];
   const int m = T.m;
+  if (m == 1) {  // a 1x1 tridiagonal is its own eigenvalue
+    if (it.k0 + tid == 0) T.eig[0] = T.d[0];
+    return;
+  }
 
   // Gershgorin bounds and the spectral scale, from the unscaled entries.
   double gl = 1e308, gu = -1e308, tn = 0.0;

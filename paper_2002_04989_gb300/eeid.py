@@ -59,7 +59,11 @@ SIGNATURES = {
                              ctypes.c_int),
     "eeid_components_batched": ([_vp, ctypes.POINTER(EeidProblem), _i64, _vp], ctypes.c_int),
     "eeid_launch_count": ([_vp], ctypes.c_int64),
+    "eeid_set_timing": ([_vp, ctypes.c_int], ctypes.c_int),
+    "eeid_phase_times": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
 }
+
+PHASES = ("tridiag", "bisect_A", "denominators", "bisect_minors", "identity")
 
 
 def library_path() -> str:
@@ -230,3 +234,16 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self.lib.eeid_launch_count(self.handle))
+
+    def eeid_launch_count(self) -> int:
+        return self.launch_count()
+
+    def eeid_set_timing(self, enable: bool = True) -> int:
+        return _check(self.lib.eeid_set_timing(self.handle, 1 if enable else 0), False)
+
+    def eeid_phase_times(self) -> dict:
+        buf = (ctypes.c_double * len(PHASES))()
+        k = self.lib.eeid_phase_times(self.handle, buf, len(PHASES))
+        if k < 0:
+            _check(k, False)
+        return {PHASES[i]: float(buf[i]) for i in range(k)}
