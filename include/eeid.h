@@ -140,6 +140,18 @@ eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* probs, in
 /* Number of kernel launches the context has enqueued so far (for accounting). */
 int64_t eeid_launch_count(const eeid_ctx* ctx);
 
+/* Tuning of the Householder kernel (K-a): matrices of size m in [m_lo, m_hi] are
+ * reduced by the variant `path` (0 = working matrix resident in shared memory,
+ * m <= 160; 1 = working matrix in a global-memory slot per CTA) with `warps` warps
+ * per CTA (path 0: 1, 2, 4, 8; path 1: 2, 4, 8).  Later rules take precedence.
+ * Results are bitwise reproducible for a fixed rule set; changing the variant of a
+ * size changes the rounding order (not the accuracy class).  EEID_ERR_INVALID for
+ * an unsupported combination. */
+eeid_status eeid_tune_tridiag(eeid_ctx* ctx, int m_lo, int m_hi, int path, int warps);
+
+/* Drop all tuning rules (back to the built-in size table). */
+eeid_status eeid_tune_reset(eeid_ctx* ctx);
+
 /* Phases of one call, in launch order, for eeid_phase_times. */
 enum {
   EEID_PHASE_TRIDIAG = 0,       /* Householder reduction of A and of the minors */

@@ -62,6 +62,8 @@ struct eeid_ctx {
   int64_t launches = 0;
   int occ_cache[2][9] = {};  // blocks/SM per (smem path, warps) at the last max_m
   int occ_m[2][9] = {};
+  struct Rule { int lo, hi; bool smem; int warps; };
+  std::vector<Rule> rules;  // tuning overrides, later ones win
   bool timing = false;
   cudaEvent_t ev[EEID_NUM_PHASES][2] = {};
   bool ran[EEID_NUM_PHASES] = {};
@@ -78,7 +80,7 @@ struct TriCfg {
   bool smem;
   int warps;
 };
-TriCfg tri_cfg(int m) {
+TriCfg tri_cfg_default(int m) {
   if (m <= 32) return {true, 1};
   if (m <= 64) return {true, 2};
   if (m <= kTridiagSmemMaxM) return {true, 4};
@@ -86,6 +88,11 @@ TriCfg tri_cfg(int m) {
   return {false, 8};
 }
 inline int cfg_key(const TriCfg& c) { return (c.smem ? 0 : 16) + c.warps; }
+
+bool cfg_supported(bool smem, int warps, int m) {
+  if (smem) return (warps == 1 || warps == 2 || warps == 4 || warps == 8) && m <= kTridiagSmemMaxM;
+  return (warps == 2 || warps == 4 || warps == 8) && m <= kTridiagMaxM;
+}
 
 struct Problem {
   const double* dA;
@@ -185,6 +192,13 @@ eeid_status ensure_stage(eeid_ctx* ctx, size_t bytes) {
   return EEID_OK;
 }
 
+TriCfg tri_cfg(const eeid_ctx* ctx, int m) {
+  for (auto it = ctx->rules.rbegin(); it != ctx->rules.rend(); ++it)
+    if (m >= it->lo && m <= it->hi && cfg_supported(it->smem, it->warps, m))
+      return {it->smem, it->warps};
+  return tri_cfg_default(m);
+}
+
 int blocks_per_sm(eeid_ctx* ctx, const TriCfg& c, int max_m) {
   int& cache = ctx->occ_cache[c.smem ? 0 : 1][c.warps];
   int& cm = ctx->occ_m[c.smem ? 0 : 1][c.warps];
@@ -235,7 +249,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   }
   // tridiagonalisation groups (one persistent launch per configuration)
   std::vector<std::vector<int>> groups(32);
-  for (size_t t = 0; t < tri.size(); ++t) groups[cfg_key(tri_cfg(tri[t].m))].push_back((int)t);
+  for (size_t t = 0; t < tri.size(); ++t) groups[cfg_key(tri_cfg(ctx, tri[t].m))].push_back((int)t);
   struct GroupPlan { TriCfg cfg; int max_m; int grid; size_t task_off, counter_off, work_off;
                      size_t slot; std::vector<int> idx; };
   std::vector<GroupPlan> gplans;
@@ -246,7 +260,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     std::stable_sort(g.idx.begin(), g.idx.end(),
                      [&](int a, int b) { return tri[a].m > tri[b].m; });  // cost-sorted
     g.max_m = tri[g.idx[0]].m;
-    g.cfg = tri_cfg(g.max_m);
+    g.cfg = tri_cfg(ctx, g.max_m);
     const int bps = blocks_per_sm(ctx, g.cfg, g.max_m);
     g.grid = (int)std::min<int64_t>((int64_t)g.idx.size(), (int64_t)ctx->sms * bps);
     g.slot = g.cfg.smem ? 0 : tridiag_global_slot_doubles(g.max_m);
@@ -454,6 +468,25 @@ void eeid_ctx_destroy(eeid_ctx* ctx) {
 }
 
 int64_t eeid_launch_count(const eeid_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+eeid_status eeid_tune_tridiag(eeid_ctx* ctx, int m_lo, int m_hi, int path, int warps) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  if (m_lo < 1 || m_hi < m_lo || (path != 0 && path != 1))
+    return fail(EEID_ERR_INVALID, "bad tuning rule");
+  if (!cfg_supported(path == 0, warps, m_hi))
+    return fail(EEID_ERR_INVALID, "unsupported variant (path %d, %d warps) for m <= %d", path, warps,
+                m_hi);
+  ctx->rules.push_back({m_lo, m_hi, path == 0, warps});
+  return EEID_OK;
+}
+
+eeid_status eeid_tune_reset(eeid_ctx* ctx) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  ctx->rules.clear();
+  return EEID_OK;
+}
 
 eeid_status eeid_set_timing(eeid_ctx* ctx, int enable) {
   eeid_status st = check_ctx(ctx);

@@ -76,8 +76,14 @@ __host__ __device__ inline Layout make_layout(bool smem, int max_m) {
   return L;
 }
 
+// Minimum resident CTAs per SM the register allocation must allow.
 template <bool SMEM, int W>
-__global__ void __launch_bounds__(W * 32) k_tridiag(TridiagLaunch P) {
+struct MinBlocks {
+  static constexpr int value = (W >= 8) ? 2 : (SMEM && W <= 2) ? 8 : 4;
+};
+
+template <bool SMEM, int W>
+__global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag(TridiagLaunch P) {
   extern __shared__ __align__(16) double sm[];
   constexpr int NT = W * 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(W * 32) k_tridiag(TridiagLaunch P) {
       for (int I = 0; I < nb; ++I) {
         if (snake_owner(I, W) != warp) continue;
         const int R0 = base + kTile * I;
-        double u = 0.0;
+        double u = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
         for (int J = 0; J <= I; ++J) {
           const int C0 = base + kTile * J;
           const int c = C0 + lane;
@@ -209,23 +215,29 @@ __global__ void __launch_bounds__(W * 32) k_tridiag(TridiagLaunch P) {
 #pragma unroll
               for (int rr = 0; rr < kTile; ++rr) dst[(size_t)rr * ld] = a[rr];
             }
+            // column half of the product: two independent chains (even / odd rows)
+            double t1 = 0.0;
 #pragma unroll
-            for (int rr = 0; rr < kTile; ++rr) t = fma(a[rr], vC[R0 + rr], t);
+            for (int rr = 0; rr < kTile; rr += 2) {
+              t = fma(a[rr], vC[R0 + rr], t);
+              t1 = fma(a[rr + 1], vC[R0 + rr + 1], t1);
+            }
+            t += t1;
             if (!SMEM) {
 #pragma unroll
               for (int rr = 0; rr < kTile; ++rr) tile[rr * kTilePad + lane] = a[rr];
             }
             tpart[((size_t)I * nbmax + J) * 32 + lane] = t;
             __syncwarp();
+            // row half: four independent chains, carried across the block-row
             const int i = R0 + lane;
-            if (SMEM) {
-              const double* rowp = S + (size_t)i * ld + C0;
+            const double* rowp = SMEM ? (S + (size_t)i * ld + C0) : (tile + lane * kTilePad);
 #pragma unroll
-              for (int cc = 0; cc < kTile; ++cc) u = fma(rowp[cc], vC[C0 + cc], u);
-            } else {
-              const double* rowp = tile + lane * kTilePad;
-#pragma unroll
-              for (int cc = 0; cc < kTile; ++cc) u = fma(rowp[cc], vC[C0 + cc], u);
+            for (int cc = 0; cc < kTile; cc += 4) {
+              u = fma(rowp[cc], vC[C0 + cc], u);
+              u1 = fma(rowp[cc + 1], vC[C0 + cc + 1], u1);
+              u2 = fma(rowp[cc + 2], vC[C0 + cc + 2], u2);
+              u3 = fma(rowp[cc + 3], vC[C0 + cc + 3], u3);
             }
             __syncwarp();
           } else {
@@ -260,7 +272,7 @@ __global__ void __launch_bounds__(W * 32) k_tridiag(TridiagLaunch P) {
             __syncwarp();
           }
         }
-        upart[I * 32 + lane] = u;
+        upart[I * 32 + lane] = (u + u1) + (u2 + u3);
       }
       __syncthreads();
       // ---- Phase E: p = tau * (row partials + column partials); gamma = tau/2 p.v

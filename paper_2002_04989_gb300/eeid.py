@@ -60,6 +60,8 @@ SIGNATURES = {
     "eeid_components_batched": ([_vp, ctypes.POINTER(EeidProblem), _i64, _vp], ctypes.c_int),
     "eeid_launch_count": ([_vp], ctypes.c_int64),
     "eeid_set_timing": ([_vp, ctypes.c_int], ctypes.c_int),
+    "eeid_tune_tridiag": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "eeid_tune_reset": ([_vp], ctypes.c_int),
     "eeid_phase_times": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
 }
 
@@ -237,6 +239,12 @@ class Context:
 
     def eeid_launch_count(self) -> int:
         return self.launch_count()
+
+    def eeid_tune_tridiag(self, m_lo: int, m_hi: int, path: int, warps: int) -> int:
+        return _check(self.lib.eeid_tune_tridiag(self.handle, m_lo, m_hi, path, warps), False)
+
+    def eeid_tune_reset(self) -> int:
+        return _check(self.lib.eeid_tune_reset(self.handle), False)
 
     def eeid_set_timing(self, enable: bool = True) -> int:
         return _check(self.lib.eeid_set_timing(self.handle, 1 if enable else 0), False)
