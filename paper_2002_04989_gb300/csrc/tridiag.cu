@@ -43,18 +43,92 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum over the CTA; every thread receives the total.  `red` alternates between two
-// halves across consecutive calls so one barrier per call suffices.
+// Sum over the CTA; every thread receives the total.  Every FP64 warp instruction
+// costs the same FP64 issue time however many lanes are active, so the partials go
+// to shared memory and one warp adds them (W + 5 FP64 instructions in total).
+// `red` holds W*32 + 1 doubles.
 template <int W>
 __device__ __forceinline__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
-  if (lane == 0) red[warp] = v;
+  red[threadIdx.x] = v;
   __syncthreads();
-  double s = 0;
+  if (warp == 0) {
+    double s = red[lane];
 #pragma unroll
-  for (int w = 0; w < W; ++w) s += red[w];
-  return s;
+    for (int w = 1; w < W; ++w) s += red[w * 32 + lane];
+    s = warp_sum(s);
+    if (lane == 0) red[W * 32] = s;
+  }
+  __syncthreads();
+  return red[W * 32];
+}
+
+// One 32x32 tile of the fused pass: rows [R0, R0+32), columns [C0, C0+32) of the
+// working matrix.  Lane l owns column C0+l in the column half and row R0+l in the
+// row half.  EDGE tiles (on the diagonal, or with rows beyond m) use predicated
+// loads and selects instead of branches, so every tile is fully unrolled;
+// positions outside the lower triangle contribute exact zeros.  UPD applies the
+// previous step's rank-2 update (absent at the first step).
+template <bool SMEM, bool EDGE, bool UPD>
+__device__ __forceinline__ void tile_step(double* __restrict__ S, int64_t ld, int m, int R0, int C0,
+                                          int lane, const double* __restrict__ vP,
+                                          const double* __restrict__ wP,
+                                          const double* __restrict__ vC, double* __restrict__ tile,
+                                          double* __restrict__ tslot, double (&u)[4]) {
+  constexpr int T = 32, TP = 33;
+  const int c = C0 + lane;
+  const bool cv = !EDGE || c < m;
+  const double vPc = UPD ? vP[c] : 0.0, wPc = UPD ? wP[c] : 0.0;
+  double t0 = 0.0, t1 = 0.0;
+  // column half in two 16-row slabs (bounded register use)
+#pragma unroll 1
+  for (int h = 0; h < T; h += 16) {
+    double a[16];
+    const double* src = S + (size_t)(R0 + h) * ld + c;
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+      const int i = R0 + h + rr;
+      const bool ok = !EDGE || (cv && i < m && i >= c);
+      a[rr] = ok ? src[(size_t)rr * ld] : 0.0;
+    }
+    if (UPD) {
+      double* dst = S + (size_t)(R0 + h) * ld + c;
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) {
+        const int i = R0 + h + rr;
+        const double x = fma(-vP[i], wPc, fma(-wP[i], vPc, a[rr]));
+        const bool ok = !EDGE || (cv && i < m && i >= c);
+        a[rr] = ok ? x : 0.0;
+        if (ok) dst[(size_t)rr * ld] = a[rr];
+      }
+    }
+    // t_c = sum_{i > c} a_ic v_i (two independent chains)
+#pragma unroll
+    for (int rr = 0; rr < 16; rr += 2) {
+      const int i = R0 + h + rr;
+      const double x0 = (!EDGE || i > c) ? a[rr] : 0.0;
+      const double x1 = (!EDGE || i + 1 > c) ? a[rr + 1] : 0.0;
+      t0 = fma(x0, vC[i], t0);
+      t1 = fma(x1, vC[i + 1], t1);
+    }
+    if (!SMEM) {
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) tile[(h + rr) * TP + lane] = a[rr];
+    }
+  }
+  *tslot = t0 + t1;
+  __syncwarp();
+  // row half: u_i += sum_{c <= i} a_ic v_c (four chains carried across the block-row)
+  const int i = R0 + lane;
+  const int ir = EDGE ? min(i, m - 1) : i;   // clamped row address for the shared copy
+  const double* rowp = SMEM ? (S + (size_t)ir * ld + C0) : (tile + lane * TP);
+#pragma unroll
+  for (int cc = 0; cc < T; ++cc) {
+    const bool ok = !EDGE || (i < m && C0 + cc <= i);
+    const double x = ok ? rowp[cc] : 0.0;
+    u[cc & 3] = fma(x, vC[C0 + cc], u[cc & 3]);
+  }
+  __syncwarp();
 }
 
 __device__ __forceinline__ int snake_owner(int I, int W) {
@@ -95,8 +169,8 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
   double* wP = vP + Ly.VM;
   double* vC = wP + Ly.VM;
   double* wC = vC + Ly.VM;
-  double* red = wC + Ly.VM;       // 2*W reduction slots
-  double* scal = red + 2 * W;     // 8 scalars
+  double* red = wC + Ly.VM;       // W*32 + 1 reduction slots (+ padding)
+  double* scal = red + W * 32 + 8;  // 8 scalars
   double* S;
   double* tpart;
   double* upart;
@@ -141,7 +215,6 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
     }
     __syncthreads();
 
-    int redsel = 0;
     for (int k = 0; k + 2 < m; ++k) {
       const int base = k + 1;
       const bool upd = (k > 0);
@@ -161,8 +234,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
           sig = fma(a, a, sig);
         }
       }
-      sig = block_sum<W>(sig, red + redsel * W);
-      redsel ^= 1;
+      sig = block_sum<W>(sig, red);
       // ---- Phase B: reflector scalars (warp 0), broadcast through shared memory.
       if (warp == 0) {
         const double alpha = scal[0];
@@ -193,86 +265,20 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
       for (int I = 0; I < nb; ++I) {
         if (snake_owner(I, W) != warp) continue;
         const int R0 = base + kTile * I;
-        double u = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+        double u[4] = {0.0, 0.0, 0.0, 0.0};
+        const bool ragged = R0 + kTile > m;
         for (int J = 0; J <= I; ++J) {
           const int C0 = base + kTile * J;
-          const int c = C0 + lane;
-          const bool full = (J < I) && (R0 + kTile <= m);
-          double t = 0.0;
-          if (full) {
-            const double vPc = upd ? vP[c] : 0.0, wPc = upd ? wP[c] : 0.0;
-            double a[kTile];
-            const double* src = S + (size_t)R0 * ld + c;
-#pragma unroll
-            for (int rr = 0; rr < kTile; ++rr) a[rr] = src[(size_t)rr * ld];
-            if (upd) {
-#pragma unroll
-              for (int rr = 0; rr < kTile; ++rr) {
-                const int i = R0 + rr;
-                a[rr] = fma(-vP[i], wPc, fma(-wP[i], vPc, a[rr]));
-              }
-              double* dst = S + (size_t)R0 * ld + c;
-#pragma unroll
-              for (int rr = 0; rr < kTile; ++rr) dst[(size_t)rr * ld] = a[rr];
-            }
-            // column half of the product: two independent chains (even / odd rows)
-            double t1 = 0.0;
-#pragma unroll
-            for (int rr = 0; rr < kTile; rr += 2) {
-              t = fma(a[rr], vC[R0 + rr], t);
-              t1 = fma(a[rr + 1], vC[R0 + rr + 1], t1);
-            }
-            t += t1;
-            if (!SMEM) {
-#pragma unroll
-              for (int rr = 0; rr < kTile; ++rr) tile[rr * kTilePad + lane] = a[rr];
-            }
-            tpart[((size_t)I * nbmax + J) * 32 + lane] = t;
-            __syncwarp();
-            // row half: four independent chains, carried across the block-row
-            const int i = R0 + lane;
-            const double* rowp = SMEM ? (S + (size_t)i * ld + C0) : (tile + lane * kTilePad);
-#pragma unroll
-            for (int cc = 0; cc < kTile; cc += 4) {
-              u = fma(rowp[cc], vC[C0 + cc], u);
-              u1 = fma(rowp[cc + 1], vC[C0 + cc + 1], u1);
-              u2 = fma(rowp[cc + 2], vC[C0 + cc + 2], u2);
-              u3 = fma(rowp[cc + 3], vC[C0 + cc + 3], u3);
-            }
-            __syncwarp();
+          double* tslot = tpart + ((size_t)I * nbmax + J) * 32 + lane;
+          if (J < I && !ragged) {
+            if (upd) tile_step<SMEM, false, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
+            else     tile_step<SMEM, false, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
           } else {
-            const bool cv = c < m;
-            const double vPc = (upd && cv) ? vP[c] : 0.0, wPc = (upd && cv) ? wP[c] : 0.0;
-            for (int rr = 0; rr < kTile; ++rr) {
-              const int i = R0 + rr;
-              if (i >= m) break;
-              if (cv && i >= c) {
-                double a = S[(size_t)i * ld + c];
-                if (upd) {
-                  a = fma(-vP[i], wPc, fma(-wP[i], vPc, a));
-                  S[(size_t)i * ld + c] = a;
-                }
-                if (!SMEM) tile[rr * kTilePad + lane] = a;
-                if (i > c) t = fma(a, vC[i], t);
-              }
-            }
-            tpart[((size_t)I * nbmax + J) * 32 + lane] = t;
-            __syncwarp();
-            const int i = R0 + lane;
-            if (i < m) {
-              const int ccmax = min(kTile, i - C0 + 1);
-              if (SMEM) {
-                const double* rowp = S + (size_t)i * ld + C0;
-                for (int cc = 0; cc < ccmax; ++cc) u = fma(rowp[cc], vC[C0 + cc], u);
-              } else {
-                const double* rowp = tile + lane * kTilePad;
-                for (int cc = 0; cc < ccmax; ++cc) u = fma(rowp[cc], vC[C0 + cc], u);
-              }
-            }
-            __syncwarp();
+            if (upd) tile_step<SMEM, true, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
+            else     tile_step<SMEM, true, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
           }
         }
-        upart[I * 32 + lane] = (u + u1) + (u2 + u3);
+        upart[I * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
       }
       __syncthreads();
       // ---- Phase E: p = tau * (row partials + column partials); gamma = tau/2 p.v
@@ -285,8 +291,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
         wC[i] = p;
         dot = fma(p, vC[i], dot);
       }
-      dot = block_sum<W>(dot, red + redsel * W);
-      redsel ^= 1;
+      dot = block_sum<W>(dot, red);
       // ---- Phase F: w = p - gamma v.
       {
         const double gamma = 0.5 * tau * dot;
@@ -329,7 +334,7 @@ size_t tridiag_global_slot_doubles(int max_m) {
 
 size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps) {
   const Layout L = make_layout(smem_path, max_m);
-  size_t d = 4 * (size_t)L.VM + 2 * warps + 8;
+  size_t d = 4 * (size_t)L.VM + (size_t)warps * 32 + 8 + 8;
   if (smem_path)
     d += (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 32;
   else
