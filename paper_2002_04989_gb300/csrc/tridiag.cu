@@ -70,11 +70,11 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // positions outside the lower triangle contribute exact zeros.  UPD applies the
 // previous step's rank-2 update (absent at the first step).
 template <bool SMEM, bool EDGE, bool UPD>
-__device__ __forceinline__ void tile_step(double* __restrict__ S, int64_t ld, int m, int R0, int C0,
-                                          int lane, const double* __restrict__ vP,
-                                          const double* __restrict__ wP,
-                                          const double* __restrict__ vC, double* __restrict__ tile,
-                                          double* __restrict__ tslot, double (&u)[4]) {
+__device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, int C0, int lane,
+                                          const double* vP, const double* wP, const double* vC,
+                                          double* tile, double* tslot, double (&u)[4]) {
+  // No __restrict__ here: S is written by this warp and read by other warps of the
+  // CTA in later steps, so its loads must stay on the coherent path.
   constexpr int T = 32, TP = 33;
   const int c = C0 + lane;
   const bool cv = !EDGE || c < m;
@@ -203,6 +203,16 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
     }
     double* __restrict__ dout = task.d;
     double* __restrict__ eout = task.e;
+
+    // Edge tiles multiply zeros by vector entries past m; those entries must be
+    // finite, so the tails [m, VM) of all four vectors are cleared per task (shared
+    // memory keeps whatever an earlier task or launch left there).
+    for (int i = m + tid; i < Ly.VM; i += NT) {
+      vP[i] = 0.0;
+      wP[i] = 0.0;
+      vC[i] = 0.0;
+      wC[i] = 0.0;
+    }
 
     // a1: the minor view -- copy the lower triangle of A without row/col `skip`.
     for (int r = warp; r < m; r += W) {
