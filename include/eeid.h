@@ -171,6 +171,29 @@ eeid_status eeid_set_timing(eeid_ctx* ctx, int enable);
  * did not run).  Returns the number of values written, or a negative status. */
 int eeid_phase_times(eeid_ctx* ctx, double* ms, int cap);
 
+/* Eigenvalues of A, like eeid_eigvals, for callers that cannot allocate device
+ * memory: for example code embedded in an application whose own memory pool owns
+ * the whole device, or code on a latency-critical path where the implicit device
+ * synchronisation of cudaMalloc/cudaFree is not acceptable.  It needs no context
+ * and calls no cudaMalloc, cudaFree or other allocating routine.  (The paper has no
+ * counterpart: this is an interface for such callers.)
+ *
+ * Scratch: one fixed file-scope device array of about 2.2 MB, present on every
+ * GPU that loads the library for the life of the process, sized for n <= 512;
+ * n > 512 returns EEID_ERR_INVALID with a message in eeid_last_error().  Every
+ * call on a device uses the same array, so calls that overlap on the GPU (for
+ * example on two streams without ordering) race and must be avoided; calls on one
+ * stream are ordered and safe.  The first call on each device looks the array's
+ * address up (with that device current) and caches it; make that first call before
+ * any stream capture.
+ *
+ * dA: device, row-major, lower triangle read, lda >= n.  d_lambda: device, n
+ * doubles, ascending.  Asynchronous on `stream` (the calling thread's current
+ * device); n == 0 is a no-op.  Results agree with eeid_eigvals within the library's
+ * eigenvalue tolerance (1e-12 * ||A||_2). */
+eeid_status eeid_eigvals_noalloc(const double* dA, int64_t lda, int64_t n, double* d_lambda,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,15 @@ namespace {
 
 thread_local std::string g_err;
 
+}  // namespace
+
+namespace eeid {
+// Lets other translation units report through eeid_last_error().
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace eeid
+
+namespace {
+
 eeid_status fail(eeid_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;

@@ -63,6 +63,7 @@ SIGNATURES = {
     "eeid_tune_tridiag": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "eeid_tune_reset": ([_vp], ctypes.c_int),
     "eeid_phase_times": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
+    "eeid_eigvals_noalloc": ([_vp, _i64, _i64, _vp, _vp], ctypes.c_int),
 }
 
 PHASES = ("tridiag", "bisect_A", "denominators", "bisect_minors", "identity")
@@ -127,6 +128,20 @@ def _mat(A):
     if A.dim() != 2 or A.shape[0] != A.shape[1] or A.stride(1) != 1:
         raise ValueError("A must be a square matrix with unit column stride (row-major)")
     return A, int(A.stride(0)) if A.shape[0] > 0 else max(1, A.shape[0])
+
+
+def eeid_eigvals_noalloc(A, out=None, stream=None):
+    """Eigenvalues of A without any device allocation by the library (n <= 512);
+    see eeid_eigvals_noalloc in include/eeid.h.  `out` may be a preallocated
+    float64 CUDA tensor of n elements."""
+    import torch
+    A, lda = _mat(A)
+    n = A.shape[0]
+    lam = out if out is not None else torch.empty(n, dtype=torch.float64, device=A.device)
+    with torch.cuda.device(A.device):
+        _check(load().eeid_eigvals_noalloc(_vp(A.data_ptr()), lda, n, _vp(lam.data_ptr()),
+                                           _stream(stream)), False)
+    return lam
 
 
 class Context:
