@@ -317,6 +317,24 @@ def run_gpu(args, world, rank, local):
     return 0
 
 
+def run_profile_case(case: str) -> int:
+    """Small, self-checking case sized for an ncu capture (a few GB on the device)."""
+    import numpy as np
+    import torch
+
+    from paper_2002_04989_gb300 import eeid, inputs
+    p = inputs.planted1024()
+    A = torch.from_numpy(p.A).cuda()
+    cols = np.arange(151)
+    ctx = eeid.Context(0)
+    for _ in range(2):
+        out = ctx.eeid_components(A, cols=cols)
+        ctx.eeid_sync()
+    err = float(np.max(np.abs(out.cpu().numpy() - (p.Q * p.Q).T[:, cols])))
+    print(f"{case}: max abs err vs Q o Q = {err:.3e}")
+    return 0 if err <= 1e-10 else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -325,9 +343,15 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--profile-case", choices=("tridiag152",), default=None,
+                    help="run only a small case for an ncu capture and exit: tridiag152 = "
+                         "A plus the minors M_0..M_150 of the planted n=1024 matrix (one "
+                         "CTA per SM), called twice")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)   # timing rule: at least 3 untimed warm-up steps
     world, rank, local = dist_env()
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_gpu(args, world, rank, local)
