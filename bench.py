@@ -317,6 +317,136 @@ def run_gpu(args, world, rank, local):
     return 0
 
 
+def tridiag_flops(sizes_and_cols) -> float:
+    """4/3 m^3 per tridiagonalisation: A (m = n) and each requested minor (m = n-1)."""
+    return sum(4.0 / 3.0 * (n ** 3 + nc * (n - 1) ** 3) for n, nc in sizes_and_cols)
+
+
+def run_other(args, world, rank, local):
+    """Lines for the other workloads: goe64 (one small matrix, all minors),
+    batch4096 (4096 matrices of uneven n in one batched call, against the plain
+    one-call-per-matrix loop) and planted4096 (n = 4096, 256 seeded columns)."""
+    import numpy as np
+    import torch
+
+    from paper_2002_04989_gb300 import eeid, inputs
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    ctx = eeid.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    extra = {}
+    if args.workload == "batch4096":
+        mats = inputs.batch4096()
+        sizes = [A.shape[0] for A in mats]
+        total = sum(sizes)
+        big = torch.empty(sum(n * n for n in sizes), dtype=torch.float64, device=dev)
+        outs = torch.empty(sum(n * n for n in sizes), dtype=torch.float64, device=dev)
+        probs, off = [], 0
+        host = np.concatenate([A.reshape(-1) for A in mats])
+        big.copy_(torch.from_numpy(host))
+        for A in mats:
+            n = A.shape[0]
+            probs.append({"A": big[off:off + n * n].view(n, n), "out": outs[off:off + n * n].view(n, n)})
+            off += n * n
+        units = float(sum(n * n for n in sizes))
+        flops = tridiag_flops([(n, n) for n in sizes])
+
+        def step():
+            ctx.eeid_components_batched(probs, stream=stream)
+            flush.fill_(1)
+
+        def plain_step():
+            for pr in probs:
+                ctx.eeid_components(pr["A"], out=pr["out"], stream=stream)
+            flush.fill_(1)
+        workload = (f"batch4096: 4096 FP64 symmetric matrices, n log-uniform on [8,256] "
+                    f"(sum n = {total}), thirds GOE / Wishart / Toeplitz(0,1), all components")
+    elif args.workload == "planted4096":
+        pl, cols = inputs.planted4096()
+        A = torch.from_numpy(pl.A).to(dev)
+        out = torch.empty((4096, 256), dtype=torch.float64, device=dev)
+        units = 4096.0 * 256
+        flops = tridiag_flops([(4096, 256)])
+
+        def step():
+            ctx.eeid_components(A, cols=cols, out=out, stream=stream)
+            flush.fill_(1)
+        plain_step = None
+        workload = ("planted4096: one FP64 n=4096 planted matrix (lam on [-10,10], min gap "
+                    "1e-4), all i x 256 seeded columns j (256 minors of size 4095)")
+    else:
+        A = torch.from_numpy(inputs.goe64()).to(dev)
+        out = torch.empty((64, 64), dtype=torch.float64, device=dev)
+        units = 64.0 * 64
+        flops = tridiag_flops([(64, 64)])
+
+        def step():
+            ctx.eeid_components(A, out=out, stream=stream)
+            flush.fill_(1)
+        plain_step = None
+        workload = "goe64: one FP64 GOE matrix n=64 (seed 0), all minors, full 64x64 grid"
+
+    for _ in range(args.warmup):
+        step()
+    st = ctx.eeid_sync(stream)
+    if args.workload == "planted4096":
+        err = float(np.max(np.abs(out.cpu().numpy() - (pl.Q * pl.Q).T[:, cols])))
+        extra["max_abs_err_vs_QoQ"] = err
+    ctx.eeid_set_timing(True)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks.start()
+    l0 = ctx.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    phases = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        phases.append(ctx.eeid_phase_times())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    launches = ctx.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    max_ms = max_over_ranks(dist, ms, dev)
+    value = aggregate_value(units, world, args.steps, max_ms)
+    ctx.eeid_set_timing(False)
+    phase_avg = {k: round(statistics.mean(ph[k] for ph in phases), 3) for k in phases[0]}
+    if plain_step is not None:
+        plain_step()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        plain_step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        extra["plain_one_call_per_matrix"] = {"value": units / (t0.elapsed_time(t1) / 1e3),
+                                              "ms_per_step": t0.elapsed_time(t1)}
+    tri = phase_avg.get("tridiag", 0.0)
+    achieved = flops / (tri / 1e3) / 1e12 if tri > 0 else None
+    peak = FP64_PEAK_GFLOPS / 1e3
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload, "components_per_step_per_gpu": units,
+                       "l2": "flushed between steps (256 MiB write)"},
+            "roofline": {"bound": "alu", "kernel": "k_tridiag (all tridiagonalisations of a step)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None},
+            "clocks": clk, "gpu_launches": launches, "phases_ms": phase_avg, "status": st}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile_case(case: str) -> int:
     """Small, self-checking case sized for an ncu capture (a few GB on the device)."""
     import numpy as np
@@ -343,6 +473,10 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--workload", choices=("planted1024", "batch4096", "planted4096", "goe64"),
+                    default="planted1024",
+                    help="planted1024 (default, the headline line); the others print a line "
+                         "of the same shape for the other workloads")
     ap.add_argument("--profile-case", choices=("tridiag152",), default=None,
                     help="run only a small case for an ncu capture and exit: tridiag152 = "
                          "A plus the minors M_0..M_150 of the planted n=1024 matrix (one "
@@ -354,6 +488,8 @@ def main(argv=None):
         return run_profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload != "planted1024":
+        return run_other(args, world, rank, local)
     return run_gpu(args, world, rank, local)
 
 
