@@ -152,6 +152,16 @@ eeid_status eeid_tune_tridiag(eeid_ctx* ctx, int m_lo, int m_hi, int path, int w
 /* Drop all tuning rules (back to the built-in size table). */
 eeid_status eeid_tune_reset(eeid_ctx* ctx);
 
+/* Autotuner for the Householder kernel.  For size buckets up to min(max_m, 1024)
+ * it times every supported variant (shared-memory or global-slot working matrix,
+ * 1-8 warps per CTA) on a full wave of synthetic m x m minors on this device,
+ * keeps the fastest per bucket, and installs the choices as tuning rules (larger
+ * sizes keep the built-in choice).  With `cache_path` non-NULL the table is read
+ * from that file when it exists and was made on the same device model, and
+ * written there after tuning.  Runs synchronously on an internal stream; takes a
+ * few seconds.  Errors: EEID_ERR_CUDA, EEID_ERR_NOMEM (workspace budget). */
+eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path);
+
 /* Phases of one call, in launch order, for eeid_phase_times. */
 enum {
   EEID_PHASE_TRIDIAG = 0,       /* Householder reduction of A and of the minors */

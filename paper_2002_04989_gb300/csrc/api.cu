@@ -73,6 +73,18 @@ struct eeid_ctx {
   int occ_m[2][9] = {};
   struct Rule { int lo, hi; bool smem; int warps; };
   std::vector<Rule> rules;  // tuning overrides, later ones win
+  int rules_version = 0;
+  // CUDA graphs of batched calls, keyed by the full description of the batch.
+  struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    char* pinned = nullptr;  // this graph's own copy of the uploaded metadata
+    int nkernels = 0;
+    uint64_t last_use = 0;
+  };
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  cudaStream_t cap_stream = nullptr;
   bool timing = false;
   cudaEvent_t ev[EEID_NUM_PHASES][2] = {};
   bool ran[EEID_NUM_PHASES] = {};
@@ -112,6 +124,8 @@ struct Problem {
   double* out;            // nrows x ncols (may be null for eig-only modes)
   double* lam_user;       // optional
   double* mu_user;        // minor-eigvals mode output (ncols x (n-1))
+  bool all_rows = false;  // rows / cols given as NULL ("all")
+  bool all_cols = false;
 };
 
 enum Mode { MODE_EIGVALS, MODE_MINORS, MODE_COMPONENTS };
@@ -162,11 +176,20 @@ eeid_status check_matrix(const double* dA, int64_t lda, int64_t n) {
   return EEID_OK;
 }
 
+void clear_graphs(eeid_ctx* ctx) {
+  for (auto& g : ctx->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.pinned) cudaFreeHost(g.pinned);
+  }
+  ctx->graphs.clear();
+}
+
 eeid_status ensure_ws(eeid_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_cap) return EEID_OK;
   if (bytes > ctx->budget)
     return fail(EEID_ERR_NOMEM, "workspace of %zu bytes exceeds the HBM budget of %zu bytes", bytes,
                 ctx->budget);
+  clear_graphs(ctx);  // graphs bake in workspace addresses
   if (ctx->ws) {
     cudaError_t e = cudaFree(ctx->ws);  // synchronises the device: prior work is done
     ctx->ws = nullptr;
@@ -218,8 +241,38 @@ int blocks_per_sm(eeid_ctx* ctx, const TriCfg& c, int max_m) {
   return cache;
 }
 
-// Plan, upload and launch the whole path for a list of problems.
-eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStream_t stream) {
+// Everything that determines a batched call's task lists and device pointers; two
+// calls with equal keys can replay the same CUDA graph.
+std::string batch_key(const std::vector<Problem>& probs, bool timing, int rules_version) {
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
+  const int hdr[3] = {timing ? 1 : 0, rules_version, (int)probs.size()};
+  put(hdr, sizeof hdr);
+  for (const Problem& P : probs) {
+    put(&P.dA, sizeof P.dA);
+    put(&P.lda, sizeof P.lda);
+    put(&P.n, sizeof P.n);
+    put(&P.out, sizeof P.out);
+    put(&P.lam_user, sizeof P.lam_user);
+    const int nr = (int)P.rows.size(), nc = (int)P.cols.size();
+    const char flags = (char)((P.all_rows ? 1 : 0) | (P.all_cols ? 2 : 0));
+    put(&flags, 1);
+    put(&nr, sizeof nr);
+    put(&nc, sizeof nc);
+    if (!P.all_rows) put(P.rows.data(), sizeof(int) * nr);
+    if (!P.all_cols) put(P.cols.data(), sizeof(int) * nc);
+  }
+  return k;
+}
+
+constexpr size_t kMaxGraphs = 8;
+
+// Plan, upload and launch the whole path for a list of problems.  With `ge` set, the
+// metadata goes to that graph entry's own pinned buffer and the upload and every
+// launch are captured (on the context's capture stream) into ge->exec instead of
+// being enqueued on `stream`; the caller then launches the graph.
+eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStream_t stream,
+                eeid_ctx::GraphEntry* ge = nullptr) {
   EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   // ---- task lists (host)
   struct TriRef { int prob; int col; int m; };  // col = -1: A itself
@@ -324,9 +377,16 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   auto D = [&](size_t off) { return (double*)(wd + off); };
 
   // ---- host image of the metadata region (counters stay zero)
-  st = ensure_stage(ctx, meta_bytes);
-  if (st != EEID_OK) return st;
-  char* img = ctx->h_stage;
+  char* img = nullptr;
+  if (ge) {
+    EEID_CK(cudaMallocHost((void**)&ge->pinned, std::max<size_t>(meta_bytes, 256)),
+            "cudaMallocHost(graph metadata)");
+    img = ge->pinned;
+  } else {
+    st = ensure_stage(ctx, meta_bytes);
+    if (st != EEID_OK) return st;
+    img = ctx->h_stage;
+  }
   memset(img, 0, meta_bytes);
   auto lam_ptr = [&](int p) { return probs[p].lam_user ? probs[p].lam_user : D(lam_off[p]); };
   auto mu_ptr = [&](int p) {
@@ -365,11 +425,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     }
     if (!iitems.empty()) memcpy(img + ii_off, iitems.data(), sizeof(IdentityItem) * iitems.size());
   }
-  EEID_CK(cudaMemcpyAsync(ws, img, meta_bytes, cudaMemcpyHostToDevice, stream),
-          "cudaMemcpyAsync(metadata)");
-  EEID_CK(cudaEventRecord(ctx->stage_ev, stream), "cudaEventRecord(stage)");
-  ctx->stage_used = true;
-
+  auto enqueue_launches = [&]() -> eeid_status {
   // ---- launches (optionally bracketed by per-phase events)
   for (int ph = 0; ph < EEID_NUM_PHASES; ++ph) ctx->ran[ph] = false;
   auto mark = [&](int ph, int which) -> cudaError_t {
@@ -421,8 +477,39 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     ctx->launches++;
     EEID_CK(mark(EEID_PHASE_IDENTITY, 1), "event");
   }
-  return EEID_OK;
+    return EEID_OK;
+  };
+  const cudaStream_t user_stream = stream;
+  const int64_t launches_before = ctx->launches;
+  if (ge) {
+    stream = ctx->cap_stream;
+    EEID_CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  }
+  EEID_CK(cudaMemcpyAsync(ws, img, meta_bytes, cudaMemcpyHostToDevice, stream),
+          "cudaMemcpyAsync(metadata)");
+  if (!ge) {
+    EEID_CK(cudaEventRecord(ctx->stage_ev, stream), "cudaEventRecord(stage)");
+    ctx->stage_used = true;
+  }
+  eeid_status lst = enqueue_launches();
+  if (ge) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(stream, &graph);
+    if (lst != EEID_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return lst;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&ge->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    ge->nkernels = (int)(ctx->launches - launches_before);
+    ctx->launches = launches_before;  // counted when the graph is launched
+    (void)user_stream;
+  }
+  return lst;
 }
+
 
 }  // namespace
 
@@ -466,6 +553,8 @@ void eeid_ctx_destroy(eeid_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  clear_graphs(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -487,6 +576,134 @@ eeid_status eeid_tune_tridiag(eeid_ctx* ctx, int m_lo, int m_hi, int path, int w
     return fail(EEID_ERR_INVALID, "unsupported variant (path %d, %d warps) for m <= %d", path, warps,
                 m_hi);
   ctx->rules.push_back({m_lo, m_hi, path == 0, warps});
+  ctx->rules_version++;
+  return EEID_OK;
+}
+
+eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  if (max_m < 1) return fail(EEID_ERR_INVALID, "max_m must be >= 1");
+  EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaDeviceProp prop;
+  EEID_CK(cudaGetDeviceProperties(&prop, ctx->device), "cudaGetDeviceProperties");
+  char header[384];
+  snprintf(header, sizeof header, "eeid-tune v1 sms=%d name=%s", prop.multiProcessorCount, prop.name);
+  const int mmax = std::min(max_m, 1024);
+  std::vector<eeid_ctx::Rule> chosen;
+  // ---- cached table
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "r");
+    if (f) {
+      char line[512];
+      bool ok = fgets(line, sizeof line, f) != nullptr;
+      if (ok) {
+        line[strcspn(line, "\r\n")] = 0;
+        ok = strcmp(line, header) == 0;
+      }
+      int lo, hi, path, w;
+      while (ok && fscanf(f, "%d %d %d %d", &lo, &hi, &path, &w) == 4) {
+        if (!cfg_supported(path == 0, w, hi) || lo < 1 || hi < lo) { ok = false; break; }
+        chosen.push_back({lo, hi, path == 0, w});
+      }
+      fclose(f);
+      if (ok && !chosen.empty() && chosen.back().hi >= mmax) {
+        for (auto& r : chosen) ctx->rules.push_back(r);
+        ctx->rules_version++;
+        return EEID_OK;
+      }
+      chosen.clear();
+    }
+  }
+  // ---- measure: for each bucket, every supported variant on a full wave of minors
+  static const int kBuckets[] = {16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 384, 512, 768, 1024};
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  EEID_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "tune stream");
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+  };
+  if (ce != cudaSuccess) { cleanup(); return cuda_fail(ce, "tune events"); }
+  int prev = 0;
+  for (int bm : kBuckets) {
+    if (prev >= mmax) break;
+    const int m = std::min(bm, mmax);
+    const int n = m + 1;
+    const double flops_task = 4.0 / 3.0 * (double)m * m * m;
+    const int T = (int)std::max<double>(2.0 * ctx->sms,
+                                        std::min<double>(64.0 * ctx->sms, 3e10 / flops_task));
+    struct Cand { TriCfg c; int grid; size_t slot; };
+    std::vector<Cand> cands;
+    for (int path = 0; path < 2; ++path)
+      for (int w : {1, 2, 4, 8}) {
+        if (!cfg_supported(path == 0, w, m)) continue;
+        TriCfg c{path == 0, w};
+        const int grid = (int)std::min<int64_t>(T, (int64_t)ctx->sms * blocks_per_sm(ctx, c, m));
+        cands.push_back({c, grid, c.smem ? 0 : tridiag_global_slot_doubles(m)});
+      }
+    size_t work_bytes = 0;
+    for (auto& c : cands) work_bytes = std::max(work_bytes, sizeof(double) * c.slot * c.grid);
+    Arena ar;
+    const size_t a_off = ar.take(sizeof(double) * (size_t)n * n);
+    const size_t t_off = ar.take(sizeof(TridiagTask) * T);
+    const size_t c_off = ar.take(sizeof(int));
+    const size_t de_off = ar.take(sizeof(double) * (size_t)T * (2 * m));
+    const size_t w_off = ar.take(work_bytes);
+    st = ensure_ws(ctx, ar.off);
+    if (st != EEID_OK) { cleanup(); return st; }
+    char* ws = ctx->ws;
+    double* A = (double*)(ws + a_off);
+    std::vector<TridiagTask> tasks(T);
+    for (int t = 0; t < T; ++t) {
+      double* d = (double*)(ws + de_off) + (size_t)t * 2 * m;
+      tasks[t] = {A, n, n, t % n, d, d + m};
+    }
+    ce = launch_fill_symmetric(A, n, n, 0x5eedULL + (unsigned long long)m, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(ws + t_off, tasks.data(), sizeof(TridiagTask) * T, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) { cleanup(); return cuda_fail(ce, "tune setup"); }
+    float best_ms = 1e30f;
+    TriCfg best = tri_cfg_default(m);
+    for (auto& c : cands) {
+      TridiagLaunch L;
+      L.tasks = (const TridiagTask*)(ws + t_off);
+      L.ntasks = T;
+      L.counter = (int*)(ws + c_off);
+      L.work = (double*)(ws + w_off);
+      L.work_stride = (int64_t)c.slot;
+      L.max_m = m;
+      L.status = ctx->d_status;
+      float msr = 0.f;
+      for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
+        ce = cudaMemsetAsync(ws + c_off, 0, sizeof(int), s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+        if (ce == cudaSuccess) ce = launch_tridiag(c.c.smem, c.c.warps, c.grid, L, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&msr, e0, e1);
+      }
+      if (ce != cudaSuccess) { cleanup(); return cuda_fail(ce, "tune run"); }
+      if (msr < best_ms) { best_ms = msr; best = c.c; }
+    }
+    chosen.push_back({prev + 1, m, best.smem, best.warps});
+    prev = m;
+  }
+  cleanup();
+  for (auto& r : chosen) ctx->rules.push_back(r);
+  ctx->rules_version++;
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "w");
+    if (f) {
+      fprintf(f, "%s\n", header);
+      for (auto& r : chosen) fprintf(f, "%d %d %d %d\n", r.lo, r.hi, r.smem ? 0 : 1, r.warps);
+      fclose(f);
+    }
+  }
   return EEID_OK;
 }
 
@@ -494,6 +711,7 @@ eeid_status eeid_tune_reset(eeid_ctx* ctx) {
   eeid_status st = check_ctx(ctx);
   if (st != EEID_OK) return st;
   ctx->rules.clear();
+  ctx->rules_version++;
   return EEID_OK;
 }
 
@@ -582,6 +800,8 @@ static eeid_status make_component_problem(const double* dA, int64_t lda, int64_t
   if (st != EEID_OK) return st;
   if (nrows > 0 && ncols > 0 && !d_out) return fail(EEID_ERR_INVALID, "d_out is NULL");
   P.dA = dA; P.lda = lda; P.n = (int)n; P.out = d_out; P.lam_user = d_lambda_opt; P.mu_user = nullptr;
+  P.all_rows = (h_rows == nullptr);
+  P.all_cols = (h_cols == nullptr);
   if (nrows == 0 || ncols == 0) P.n = 0;  // no-op problem
   return EEID_OK;
 }
@@ -613,7 +833,47 @@ eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* in, int64
       return st;
     }
   }
-  return run(ctx, probs, MODE_COMPONENTS, (cudaStream_t)stream);
+  // Replay the captured graph of an identical earlier batch, or capture a new one.
+  EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::string key = batch_key(probs, ctx->timing, ctx->rules_version);
+  for (auto& g : ctx->graphs) {
+    if (g.key == key) {
+      g.last_use = ++ctx->graph_clock;
+      EEID_CK(cudaGraphLaunch(g.exec, s), "cudaGraphLaunch");
+      ctx->launches += g.nkernels;
+      return EEID_OK;
+    }
+  }
+  if (!ctx->cap_stream)
+    EEID_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream");
+  if (ctx->graphs.size() >= kMaxGraphs) {
+    size_t victim = 0;
+    for (size_t i = 1; i < ctx->graphs.size(); ++i)
+      if (ctx->graphs[i].last_use < ctx->graphs[victim].last_use) victim = i;
+    EEID_CK(cudaStreamSynchronize(s), "sync before graph eviction");
+    cudaGraphExecDestroy(ctx->graphs[victim].exec);
+    cudaFreeHost(ctx->graphs[victim].pinned);
+    ctx->graphs.erase(ctx->graphs.begin() + victim);
+  }
+  eeid_ctx::GraphEntry ge;
+  ge.key = std::move(key);
+  st = run(ctx, probs, MODE_COMPONENTS, s, &ge);
+  if (st != EEID_OK || !ge.exec) {
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    if (ge.pinned) cudaFreeHost(ge.pinned);
+    return st;
+  }
+  ge.last_use = ++ctx->graph_clock;
+  cudaError_t e = cudaGraphLaunch(ge.exec, s);
+  if (e != cudaSuccess) {
+    cudaGraphExecDestroy(ge.exec);
+    cudaFreeHost(ge.pinned);
+    return cuda_fail(e, "cudaGraphLaunch");
+  }
+  ctx->launches += ge.nkernels;
+  ctx->graphs.push_back(std::move(ge));
+  return EEID_OK;
 }
 
 eeid_status eeid_components_host(eeid_ctx* ctx, const double* hA, int64_t lda, int64_t n,

@@ -99,4 +99,8 @@ constexpr int kIdentityThreads = 128;
 cudaError_t launch_identity(const IdentityProblem* probs, const IdentityItem* items, int nitems,
                             int max_n, cudaStream_t s);
 
+// Deterministic symmetric matrix (uniform [-0.5, 0.5) entries) for the autotuner.
+cudaError_t launch_fill_symmetric(double* A, int n, int64_t lda, unsigned long long seed,
+                                  cudaStream_t s);
+
 }  // namespace eeid

@@ -62,6 +62,7 @@ SIGNATURES = {
     "eeid_set_timing": ([_vp, ctypes.c_int], ctypes.c_int),
     "eeid_tune_tridiag": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "eeid_tune_reset": ([_vp], ctypes.c_int),
+    "eeid_autotune": ([_vp, ctypes.c_int, ctypes.c_char_p], ctypes.c_int),
     "eeid_phase_times": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
     "eeid_eigvals_noalloc": ([_vp, _i64, _i64, _vp, _vp], ctypes.c_int),
 }
@@ -257,6 +258,10 @@ class Context:
 
     def eeid_tune_tridiag(self, m_lo: int, m_hi: int, path: int, warps: int) -> int:
         return _check(self.lib.eeid_tune_tridiag(self.handle, m_lo, m_hi, path, warps), False)
+
+    def eeid_autotune(self, max_m: int = 1024, cache_path: str | None = None) -> int:
+        path = cache_path.encode() if cache_path else None
+        return _check(self.lib.eeid_autotune(self.handle, int(max_m), path), False)
 
     def eeid_tune_reset(self) -> int:
         return _check(self.lib.eeid_tune_reset(self.handle), False)

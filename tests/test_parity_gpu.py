@@ -268,3 +268,57 @@ def test_batched_matches_single_bitwise(torch_cuda, ctx):
     for (o, lam), p in zip(singles, probs):
         assert np.array_equal(p["out"].cpu().numpy(), o)
         assert np.array_equal(p["lam"].cpu().numpy(), lam)
+
+
+def test_batched_graph_replay_reads_live_inputs(torch_cuda, ctx, oracle_mod):
+    """A repeated batch replays its captured CUDA graph (same kernel count, no new
+    capture) and recomputes from the current contents of the input buffers."""
+    torch = torch_cuda
+    mats = [inputs.goe(n, 500 + n) for n in (9, 40, 77)]
+    probs = [{"A": dev(torch, A), "out": torch.empty(A.shape, dtype=torch.float64, device="cuda")}
+             for A in mats]
+    ctx.eeid_components_batched(probs)
+    ctx.eeid_sync()
+    l1 = ctx.launch_count()
+    first = [p["out"].cpu().numpy().copy() for p in probs]
+    ctx.eeid_components_batched(probs)          # replay
+    ctx.eeid_sync()
+    l2 = ctx.launch_count()
+    assert l2 - l1 > 0
+    for p, f in zip(probs, first):
+        assert np.array_equal(p["out"].cpu().numpy(), f)
+    # new matrix contents in the same buffers -> the replay must see them
+    newA = inputs.wishart(40, 9)
+    probs[1]["A"].copy_(torch.from_numpy(newA))
+    ctx.eeid_components_batched(probs)
+    ctx.eeid_sync()
+    assert ctx.launch_count() - l2 == l2 - l1    # same graph, same kernel count
+    ref, lam_ref, _ = oracle_mod.components(newA, method=0, want_eigs=True)
+    assert np.max(np.abs(probs[1]["out"].cpu().numpy() - ref)) <= vsq_bar(lam_ref)
+
+
+def test_autotune_table_and_cache(torch_cuda, tmp_path, oracle_mod):
+    """The autotuner installs per-size variants, writes its table, and a second
+    context that loads the table computes bitwise the same results."""
+    from paper_2002_04989_gb300 import eeid
+    path = str(tmp_path / "tune.txt")
+    A = inputs.goe(150, 31)
+    c1 = eeid.Context(0)
+    c2 = eeid.Context(0)
+    try:
+        c1.eeid_autotune(256, path)
+        lines = open(path).read().splitlines()
+        assert lines[0].startswith("eeid-tune v1") and len(lines) > 3
+        assert int(lines[-1].split()[1]) >= 256
+        c2.eeid_autotune(256, path)              # loads the cached table
+        o1 = c1.eeid_components(dev(torch_cuda, A)).cpu().numpy()
+        c1.eeid_sync()
+        o2 = c2.eeid_components(dev(torch_cuda, A)).cpu().numpy()
+        c2.eeid_sync()
+        assert np.array_equal(o1, o2)
+        ref, lam_ref, _ = oracle_mod.components(A, rows=[0, 75, 149], cols=[0, 75, 149],
+                                                method=0, want_eigs=True)
+        assert np.max(np.abs(o1[np.ix_([0, 75, 149], [0, 75, 149])] - ref)) <= vsq_bar(lam_ref)
+    finally:
+        c1.close()
+        c2.close()
