@@ -431,7 +431,9 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   auto mark = [&](int ph, int which) -> cudaError_t {
     if (!ctx->timing) return cudaSuccess;
     if (which == 1) ctx->ran[ph] = true;
-    return cudaEventRecord(ctx->ev[ph][which], stream);
+    // inside a capture the record must become a graph node (external event)
+    return ge ? cudaEventRecordWithFlags(ctx->ev[ph][which], stream, cudaEventRecordExternal)
+              : cudaEventRecord(ctx->ev[ph][which], stream);
   };
   EEID_CK(mark(EEID_PHASE_TRIDIAG, 0), "event");
   for (auto& g : gplans) {

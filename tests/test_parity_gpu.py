@@ -322,3 +322,19 @@ def test_autotune_table_and_cache(torch_cuda, tmp_path, oracle_mod):
     finally:
         c1.close()
         c2.close()
+
+
+def test_phase_times_with_graphs(torch_cuda, ctx):
+    """Per-phase timing works for captured batched calls (events become graph nodes)."""
+    torch = torch_cuda
+    A = inputs.goe(60, 77)
+    probs = [{"A": dev(torch, A), "out": torch.empty((60, 60), dtype=torch.float64, device="cuda")}]
+    ctx.eeid_set_timing(True)
+    try:
+        for _ in range(2):
+            ctx.eeid_components_batched(probs)
+            ph = ctx.eeid_phase_times()
+            assert ph["tridiag"] > 0 and ph["bisect_minors"] > 0 and ph["identity"] > 0
+    finally:
+        ctx.eeid_set_timing(False)
+    ctx.eeid_sync()
