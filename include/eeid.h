@@ -137,6 +137,11 @@ typedef struct {
 eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* probs, int64_t count,
                                     void* stream);
 
+/* Enable (default) or disable CUDA-graph capture and replay for
+ * eeid_components_batched.  With graphs off every batched call plans and launches
+ * directly (better when batch shapes never repeat, as in serving). */
+eeid_status eeid_set_graphs(eeid_ctx* ctx, int enable);
+
 /* Number of kernel launches the context has enqueued so far (for accounting). */
 int64_t eeid_launch_count(const eeid_ctx* ctx);
 
@@ -180,6 +185,77 @@ eeid_status eeid_set_timing(eeid_ctx* ctx, int enable);
  * in milliseconds into ms[0 .. min(cap, EEID_NUM_PHASES)) (0 for phases that call
  * did not run).  Returns the number of values written, or a negative status. */
 int eeid_phase_times(eeid_ctx* ctx, double* ms, int cap);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop with continuous batching.  Callers on any thread submit a host
+ * matrix and the components they want; a scheduler thread admits requests in
+ * arrival order while the device budget allows, merges all admitted waiting
+ * requests into one batched launch (the work of eeid_components_batched), and keeps
+ * up to `max_inflight` batches on the GPU at once, each on its own stream and
+ * workspace, so requests arriving while a batch runs start as soon as a slot and
+ * memory free up and overlap it.  A request's matrix, output and eigenvalues stay
+ * resident on the device until its results are copied back.  Each result is
+ * bitwise the same as eeid_components on that matrix alone.  (The paper serves one
+ * component per call; this is the build's own serving form of Eq. 1.) */
+typedef struct eeid_server eeid_server;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* device memory for the server (0 = half of free): half for
+                              resident requests, half split over the batch workspaces */
+  int max_batch;           /* most requests merged into one batch (0 = 64) */
+  int max_inflight;        /* batches on the GPU at once (0 = 2) */
+  int max_pending;         /* waiting requests before submit blocks / returns BUSY (0 = 4096) */
+} eeid_server_opts;
+
+typedef struct {
+  double queue_ms;          /* submit -> batch launch */
+  double total_ms;          /* submit -> results in the caller's buffers */
+  int64_t batch_id;         /* batch that served the request (-1 if none) */
+  int64_t batch_requests;   /* requests in that batch */
+} eeid_req_stats;
+
+typedef struct {
+  int64_t pending;                 /* requests waiting for admission */
+  int64_t inflight_batches;        /* batches on the GPU now */
+  int64_t batches_launched;        /* since creation */
+  int64_t max_overlapping_batches; /* most batches seen on the GPU at once */
+  int64_t device_bytes_in_use;     /* resident request memory */
+  int64_t device_budget_bytes;
+} eeid_server_info_t;
+
+/* Start a server on `device` (opts may be NULL for defaults). */
+eeid_status eeid_server_create(int device, const eeid_server_opts* opts, eeid_server** out);
+
+/* Stop: cancels requests not yet admitted, waits for the batches on the GPU, frees
+ * everything (including results nobody waited for).  No other call on the server
+ * may be in progress. */
+void eeid_server_destroy(eeid_server* srv);
+
+/* Submit |v_ij|^2 for all i and j in h_cols (NULL = all j, ncols = n) of the host
+ * matrix hA (row-major, lda >= n, lower triangle read; copied at submit, so hA may be
+ * reused at once).  Results will be written to h_out (n x ncols, row-major) and, if
+ * non-NULL, the eigenvalues to h_lambda_opt (n); both must stay valid until
+ * eeid_server_wait returns for the ticket.  With the queue full, nonblocking != 0
+ * returns EEID_ERR_BUSY, otherwise the call waits for room.  A request larger than
+ * the device budget returns EEID_ERR_NOMEM.  *ticket identifies the request. */
+eeid_status eeid_server_submit(eeid_server* srv, const double* hA, int64_t lda, int64_t n,
+                               const int64_t* h_cols, int64_t ncols, double* h_out,
+                               double* h_lambda_opt, int nonblocking, uint64_t* ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a request; on completion fills stats
+ * (may be NULL), releases the ticket and returns the request's status (warnings
+ * included; warnings are those of its whole batch).  EEID_ERR_TIMEOUT leaves the
+ * request in place; EEID_ERR_CANCELLED if it was cancelled; EEID_ERR_NOT_FOUND for
+ * an unknown or already-waited ticket. */
+eeid_status eeid_server_wait(eeid_server* srv, uint64_t ticket, int64_t timeout_ms,
+                             eeid_req_stats* stats);
+
+/* Cancel a request that has not been admitted yet (EEID_ERR_BUSY once it runs).
+ * Its wait then returns EEID_ERR_CANCELLED. */
+eeid_status eeid_server_cancel(eeid_server* srv, uint64_t ticket);
+
+/* Counters of the serving loop. */
+eeid_status eeid_server_info(eeid_server* srv, eeid_server_info_t* info);
 
 /* Eigenvalues of A, like eeid_eigvals, for callers that cannot allocate device
  * memory: for example code embedded in an application whose own memory pool owns

@@ -85,6 +85,7 @@ struct eeid_ctx {
   std::vector<GraphEntry> graphs;
   uint64_t graph_clock = 0;
   cudaStream_t cap_stream = nullptr;
+  bool graphs_enabled = true;
   bool timing = false;
   cudaEvent_t ev[EEID_NUM_PHASES][2] = {};
   bool ran[EEID_NUM_PHASES] = {};
@@ -326,7 +327,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     const int bps = blocks_per_sm(ctx, g.cfg, g.max_m);
     g.grid = (int)std::min<int64_t>((int64_t)g.idx.size(), (int64_t)ctx->sms * bps);
     g.slot = g.cfg.smem ? 0 : tridiag_global_slot_doubles(g.max_m);
-    g.work_off = g.cfg.smem ? 0 : dat.take(sizeof(double) * g.slot * g.grid);
+    g.work_off = 0;  // assigned after the rest of the layout (see below)
     g.task_off = meta.take(sizeof(TridiagTask) * g.idx.size());
     g.counter_off = meta.take(sizeof(int));
     gplans.push_back(std::move(g));
@@ -370,6 +371,30 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     ii_off = meta.take(sizeof(IdentityItem) * std::max<size_t>(iitems.size(), 1));
   }
   const size_t meta_bytes = meta.off;
+  // Working slots of the global-memory groups go last.  If the whole layout would
+  // exceed the context's budget, fewer persistent CTAs (slots) are used: the same
+  // tasks in more rounds, with identical per-task arithmetic.
+  {
+    size_t slots_total = 0;
+    for (auto& g : gplans) slots_total += sizeof(double) * g.slot * g.grid;
+    const size_t fixed = meta_bytes + dat.off + kAlign * (gplans.size() + 1);
+    if (slots_total > 0 && fixed + slots_total > ctx->budget) {
+      if (fixed >= ctx->budget)
+        return fail(EEID_ERR_NOMEM, "task data of %zu bytes exceeds the HBM budget of %zu bytes",
+                    fixed, ctx->budget);
+      const double scale = (double)(ctx->budget - fixed) / (double)slots_total;
+      for (auto& g : gplans) {
+        if (g.cfg.smem) continue;
+        const int ng = (int)((double)g.grid * scale);
+        if (ng < 1)
+          return fail(EEID_ERR_NOMEM, "one working slot (%zu bytes) does not fit the HBM budget",
+                      sizeof(double) * g.slot);
+        g.grid = ng;
+      }
+    }
+    for (auto& g : gplans)
+      if (!g.cfg.smem) g.work_off = dat.take(sizeof(double) * g.slot * g.grid);
+  }
   eeid_status st = ensure_ws(ctx, meta_bytes + dat.off);
   if (st != EEID_OK) return st;
   char* ws = ctx->ws;
@@ -709,6 +734,18 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
   return EEID_OK;
 }
 
+eeid_status eeid_set_graphs(eeid_ctx* ctx, int enable) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  ctx->graphs_enabled = enable != 0;
+  if (!ctx->graphs_enabled) {
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    clear_graphs(ctx);
+  }
+  return EEID_OK;
+}
+
 eeid_status eeid_tune_reset(eeid_ctx* ctx) {
   eeid_status st = check_ctx(ctx);
   if (st != EEID_OK) return st;
@@ -838,6 +875,7 @@ eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* in, int64
   // Replay the captured graph of an identical earlier batch, or capture a new one.
   EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
+  if (!ctx->graphs_enabled) return run(ctx, probs, MODE_COMPONENTS, s);
   std::string key = batch_key(probs, ctx->timing, ctx->rules_version);
   for (auto& g : ctx->graphs) {
     if (g.key == key) {

@@ -41,6 +41,22 @@ class EeidError(RuntimeError):
         self.status = status
 
 
+class EeidServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int),
+                ("max_inflight", ctypes.c_int), ("max_pending", ctypes.c_int)]
+
+
+class EeidReqStats(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("batch_id", ctypes.c_int64), ("batch_requests", ctypes.c_int64)]
+
+
+class EeidServerInfo(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_int64), ("inflight_batches", ctypes.c_int64),
+                ("batches_launched", ctypes.c_int64), ("max_overlapping_batches", ctypes.c_int64),
+                ("device_bytes_in_use", ctypes.c_int64), ("device_budget_bytes", ctypes.c_int64)]
+
+
 class EeidProblem(ctypes.Structure):
     _fields_ = [("dA", _vp), ("lda", _i64), ("n", _i64), ("h_rows", _i64p), ("nrows", _i64),
                 ("h_cols", _i64p), ("ncols", _i64), ("d_out", _vp), ("d_lambda", _vp)]
@@ -65,6 +81,15 @@ SIGNATURES = {
     "eeid_autotune": ([_vp, ctypes.c_int, ctypes.c_char_p], ctypes.c_int),
     "eeid_phase_times": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
     "eeid_eigvals_noalloc": ([_vp, _i64, _i64, _vp, _vp], ctypes.c_int),
+    "eeid_set_graphs": ([_vp, ctypes.c_int], ctypes.c_int),
+    "eeid_server_create": ([ctypes.c_int, ctypes.POINTER(EeidServerOpts), ctypes.POINTER(_vp)],
+                           ctypes.c_int),
+    "eeid_server_destroy": ([_vp], None),
+    "eeid_server_submit": ([_vp, _vp, _i64, _i64, _i64p, _i64, _vp, _vp, ctypes.c_int,
+                            ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "eeid_server_wait": ([_vp, ctypes.c_uint64, _i64, ctypes.POINTER(EeidReqStats)], ctypes.c_int),
+    "eeid_server_cancel": ([_vp, ctypes.c_uint64], ctypes.c_int),
+    "eeid_server_info": ([_vp, ctypes.POINTER(EeidServerInfo)], ctypes.c_int),
 }
 
 PHASES = ("tridiag", "bisect_A", "denominators", "bisect_minors", "identity")
@@ -250,6 +275,9 @@ class Context:
         return _check(self.lib.eeid_components_batched(self.handle, arr, len(problems),
                                                        _stream(stream)))
 
+    def eeid_set_graphs(self, enable: bool = True) -> int:
+        return _check(self.lib.eeid_set_graphs(self.handle, 1 if enable else 0), False)
+
     def launch_count(self) -> int:
         return int(self.lib.eeid_launch_count(self.handle))
 
@@ -275,3 +303,70 @@ class Context:
         if k < 0:
             _check(k, False)
         return {PHASES[i]: float(buf[i]) for i in range(k)}
+
+
+class Server:
+    """The serving loop (eeid_server_*): continuous batching of requests on one GPU.
+    submit() copies the host matrix and returns a ticket; wait() blocks for that
+    request and returns (out, lam, stats)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_batch: int = 0,
+                 max_inflight: int = 0, max_pending: int = 0):
+        self.lib = load()
+        opts = EeidServerOpts(hbm_budget_bytes, max_batch, max_inflight, max_pending)
+        h = _vp()
+        _check(self.lib.eeid_server_create(int(device), ctypes.byref(opts), ctypes.byref(h)), False)
+        self.handle = h
+        self._bufs = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.eeid_server_destroy(self.handle)
+            self.handle = None
+            self._bufs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def eeid_server_submit(self, A: np.ndarray, cols=None, nonblocking: bool = False) -> int:
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        n = A.shape[0]
+        cp, nc, keep = _idx(cols)
+        nc = n if cp is None else nc
+        out = np.empty((n, nc))
+        lam = np.empty(n)
+        t = ctypes.c_uint64()
+        _check(self.lib.eeid_server_submit(self.handle, A.ctypes.data_as(_vp), n, n, cp, nc,
+                                           out.ctypes.data_as(_vp), lam.ctypes.data_as(_vp),
+                                           1 if nonblocking else 0, ctypes.byref(t)), False)
+        self._bufs[t.value] = (out, lam)
+        return t.value
+
+    def eeid_server_wait(self, ticket: int, timeout_ms: int = -1):
+        st = EeidReqStats()
+        status = self.lib.eeid_server_wait(self.handle, ctypes.c_uint64(ticket), int(timeout_ms),
+                                           ctypes.byref(st))
+        if status == EEID_ERR_TIMEOUT:
+            raise EeidError(status, last_error())
+        out, lam = self._bufs.pop(ticket, (None, None))
+        _check(status)
+        return out, lam, {"queue_ms": st.queue_ms, "total_ms": st.total_ms,
+                          "batch_id": st.batch_id, "batch_requests": st.batch_requests,
+                          "status": status}
+
+    def eeid_server_cancel(self, ticket: int) -> int:
+        return _check(self.lib.eeid_server_cancel(self.handle, ctypes.c_uint64(ticket)), False)
+
+    def eeid_server_info(self) -> dict:
+        info = EeidServerInfo()
+        _check(self.lib.eeid_server_info(self.handle, ctypes.byref(info)), False)
+        return {f: getattr(info, f) for f, _ in EeidServerInfo._fields_}

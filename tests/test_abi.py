@@ -71,3 +71,12 @@ def test_ctx_create_reports_missing_gpu(lib):
     st = lib.eeid_ctx_create(0, 0, ctypes.byref(h))
     assert st == eeid.EEID_ERR_CUDA
     assert h.value is None
+
+
+def test_server_create_reports_missing_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.eeid_server_create(0, None, ctypes.byref(h)) == eeid.EEID_ERR_CUDA
+    assert lib.eeid_server_submit(None, None, 1, 1, None, 1, None, None, 0, None) == eeid.EEID_ERR_INVALID

@@ -1,0 +1,118 @@
+"""The serving loop (eeid_server_*): continuous batching, overlap of batches on the
+device, admission by device budget, cancellation and bounded waits.  Every
+failure here is made on the host (a cancelled request, a wait that runs out, a
+budget refusal); no GPU fault is involved."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2002_04989_gb300 import eeid, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    return torch
+
+
+def solo(torch, A, cols=None):
+    ctx = eeid.Context(0)
+    try:
+        lam = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+        out = ctx.eeid_components(torch.from_numpy(A).cuda(), cols=cols, lam=lam)
+        ctx.eeid_sync()
+        return out.cpu().numpy(), lam.cpu().numpy()
+    finally:
+        ctx.close()
+
+
+def test_results_same_alone_and_in_the_mix(torch_cuda):
+    """Requests submitted from two threads at once are merged into shared batches;
+    each result is bitwise the result of computing that matrix alone."""
+    reqs = []
+    for rid in range(14):
+        g = np.random.default_rng(rid)
+        n = int(g.integers(16, 260))
+        A = inputs.goe(n, 700 + rid) if rid % 2 else inputs.planted(n, 800 + rid, gap=1e-3).A
+        cols = None if rid % 3 else np.sort(g.choice(n, min(n, 1 + rid), replace=False))
+        reqs.append((A, cols))
+    tickets = [None] * len(reqs)
+    with eeid.Server(0, max_batch=8, max_inflight=2) as srv:
+        def sub(lo, hi):
+            for k in range(lo, hi):
+                tickets[k] = srv.eeid_server_submit(reqs[k][0], cols=reqs[k][1])
+        th = [threading.Thread(target=sub, args=(0, 7)), threading.Thread(target=sub, args=(7, 14))]
+        [t.start() for t in th]
+        [t.join() for t in th]
+        results = [srv.eeid_server_wait(t) for t in tickets]
+        info = srv.eeid_server_info()
+    assert info["batches_launched"] < len(reqs)          # requests were merged
+    assert max(r[2]["batch_requests"] for r in results) > 1
+    for (A, cols), (out, lam, st) in zip(reqs, results):
+        o_ref, l_ref = solo(torch_cuda, A, cols)
+        assert np.array_equal(out, o_ref) and np.array_equal(lam, l_ref)
+
+
+def test_arrivals_overlap_a_running_batch(torch_cuda):
+    """Small requests that arrive while a large batch runs start on the second slot
+    and finish before it (continuous batching, not a FIFO queue)."""
+    big = inputs.planted(1400, 5, gap=1e-4).A
+    smalls = [inputs.goe(40 + 10 * k, 60 + k) for k in range(4)]
+    with eeid.Server(0, max_batch=16, max_inflight=2) as srv:
+        tb = srv.eeid_server_submit(big)
+        time.sleep(0.05)
+        ts = [srv.eeid_server_submit(A) for A in smalls]
+        small_res = [srv.eeid_server_wait(t) for t in ts]
+        t_small_done = time.perf_counter()
+        big_res = srv.eeid_server_wait(tb)
+        t_big_done = time.perf_counter()
+        info = srv.eeid_server_info()
+    assert info["max_overlapping_batches"] == 2
+    assert t_small_done < t_big_done
+    assert all(r[2]["batch_id"] != big_res[2]["batch_id"] for r in small_res)
+    for A, (out, lam, st) in zip(smalls, small_res):
+        o_ref, _ = solo(torch_cuda, A)
+        assert np.array_equal(out, o_ref)
+
+
+def test_cancel_and_bounded_wait(torch_cuda):
+    big = inputs.planted(1200, 6, gap=1e-4).A
+    small = inputs.goe(30, 3)
+    with eeid.Server(0, max_batch=1, max_inflight=1) as srv:
+        tb = srv.eeid_server_submit(big)
+        time.sleep(0.05)
+        ts = srv.eeid_server_submit(small)
+        assert srv.eeid_server_cancel(ts) == 0          # still waiting for admission
+        with pytest.raises(eeid.EeidError) as ei:
+            srv.eeid_server_wait(ts)
+        assert ei.value.status == eeid.EEID_ERR_CANCELLED
+        with pytest.raises(eeid.EeidError) as ei:
+            srv.eeid_server_wait(tb, timeout_ms=0)       # bounded wait runs out
+        assert ei.value.status == eeid.EEID_ERR_TIMEOUT
+        out, lam, st = srv.eeid_server_wait(tb)          # the request is still there
+        assert out.shape == (1200, 1200) and np.isfinite(out).all()
+        with pytest.raises(eeid.EeidError) as ei:
+            srv.eeid_server_wait(tb)
+        assert ei.value.status == eeid.EEID_ERR_NOT_FOUND
+
+
+def test_budget_refusal_and_busy(torch_cuda):
+    with eeid.Server(0, hbm_budget_bytes=64 << 20, max_pending=1, max_inflight=1,
+                     max_batch=1) as srv:
+        with pytest.raises(eeid.EeidError) as ei:       # 2 x 33.5 MB > 32 MB request budget
+            srv.eeid_server_submit(inputs.goe(2048, 1))
+        assert ei.value.status == eeid.EEID_ERR_NOMEM
+        t1 = srv.eeid_server_submit(inputs.goe(900, 2))
+        t2 = srv.eeid_server_submit(inputs.goe(900, 3))  # may wait for queue room
+        with pytest.raises(eeid.EeidError) as ei:
+            for _ in range(50):                          # queue of one: a non-blocking
+                srv.eeid_server_submit(inputs.goe(900, 4), nonblocking=True)  # submit fails
+        assert ei.value.status == eeid.EEID_ERR_BUSY
+        for t in (t1, t2):
+            srv.eeid_server_wait(t)
