@@ -108,11 +108,12 @@ def test_budget_refusal_and_busy(torch_cuda):
         with pytest.raises(eeid.EeidError) as ei:       # 2 x 33.5 MB > 32 MB request budget
             srv.eeid_server_submit(inputs.goe(2048, 1))
         assert ei.value.status == eeid.EEID_ERR_NOMEM
-        t1 = srv.eeid_server_submit(inputs.goe(900, 2))
-        t2 = srv.eeid_server_submit(inputs.goe(900, 3))  # may wait for queue room
+        # a 32 MB workspace per batch still runs n = 400 (fewer persistent CTAs)
+        t1 = srv.eeid_server_submit(inputs.goe(400, 2))
+        t2 = srv.eeid_server_submit(inputs.goe(400, 3))  # may wait for queue room
         with pytest.raises(eeid.EeidError) as ei:
             for _ in range(50):                          # queue of one: a non-blocking
-                srv.eeid_server_submit(inputs.goe(900, 4), nonblocking=True)  # submit fails
+                srv.eeid_server_submit(inputs.goe(400, 4), nonblocking=True)  # submit fails
         assert ei.value.status == eeid.EEID_ERR_BUSY
         for t in (t1, t2):
             srv.eeid_server_wait(t)
