@@ -131,76 +131,6 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
   __syncwarp();
 }
 
-// ---- global-slot variant: tiles staged through a double-buffered shared buffer
-// with cp.async (sm_80+ asynchronous copies), so the next tile streams in while the
-// current one is computed.  Positions outside the lower triangle (or beyond m) are
-// zero-filled by the copy itself (source size 0).
-
-__device__ __forceinline__ void cp_async8(double* dst_smem, const double* src, bool valid) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-  const int n = valid ? 8 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Issue the copies of tile (R0, C0) into buf (32 rows x 33 doubles).
-__device__ __forceinline__ void tile_issue(const double* S, int64_t ld, int m, int R0, int C0,
-                                           int lane, double* buf, bool edge) {
-  const int c = C0 + lane;
-  const double* src = S + (size_t)R0 * ld + c;
-#pragma unroll 8
-  for (int rr = 0; rr < 32; ++rr) {
-    const int i = R0 + rr;
-    const bool ok = !edge || (c < m && i < m && i >= c);
-    cp_async8(buf + rr * 33 + lane, ok ? src + (size_t)rr * ld : S, ok);
-  }
-}
-
-// The fused update + product on a staged tile (see tile_step for the roles).
-template <bool EDGE, bool UPD>
-__device__ __forceinline__ void tile_staged(double* S, int64_t ld, int m, int R0, int C0, int lane,
-                                            const double* vP, const double* wP, const double* vC,
-                                            double* buf, double* tslot, double (&u)[4]) {
-  constexpr int T = 32, TP = 33;
-  const int c = C0 + lane;
-  const bool cv = !EDGE || c < m;
-  const double vPc = UPD ? vP[c] : 0.0, wPc = UPD ? wP[c] : 0.0;
-  double t0 = 0.0, t1 = 0.0;
-  double* dst = S + (size_t)R0 * ld + c;
-#pragma unroll 8
-  for (int rr = 0; rr < T; rr += 2) {
-    const int i = R0 + rr;
-    double a0 = buf[rr * TP + lane], a1 = buf[(rr + 1) * TP + lane];
-    if (UPD) {
-      const bool ok0 = !EDGE || (cv && i < m && i >= c);
-      const bool ok1 = !EDGE || (cv && i + 1 < m && i + 1 >= c);
-      const double x0 = fma(-vP[i], wPc, fma(-wP[i], vPc, a0));
-      const double x1 = fma(-vP[i + 1], wPc, fma(-wP[i + 1], vPc, a1));
-      a0 = ok0 ? x0 : 0.0;
-      a1 = ok1 ? x1 : 0.0;
-      if (ok0) dst[(size_t)rr * ld] = a0;
-      if (ok1) dst[(size_t)(rr + 1) * ld] = a1;
-      buf[rr * TP + lane] = a0;
-      buf[(rr + 1) * TP + lane] = a1;
-    }
-    t0 = fma((!EDGE || i > c) ? a0 : 0.0, vC[i], t0);
-    t1 = fma((!EDGE || i + 1 > c) ? a1 : 0.0, vC[i + 1], t1);
-  }
-  *tslot = t0 + t1;
-  __syncwarp();
-  const int i = R0 + lane;
-  const double* rowp = buf + lane * TP;
-#pragma unroll
-  for (int cc = 0; cc < T; ++cc) {
-    const bool ok = !EDGE || (i < m && C0 + cc <= i);
-    const double x = ok ? rowp[cc] : 0.0;
-    u[cc & 3] = fma(x, vC[C0 + cc], u[cc & 3]);
-  }
-  __syncwarp();
-}
-
 __device__ __forceinline__ int snake_owner(int I, int W) {
   const int q = I / W, r = I % W;
   return (q & 1) ? (W - 1 - r) : r;
@@ -254,7 +184,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
     S = slot;
     tpart = S + (size_t)P.max_m * ld;
     upart = tpart + (size_t)nbmax * nbmax * 32;
-    tile = scal + 8 + warp * (2 * kTile * kTilePad);   // two staging buffers per warp
+    tile = scal + 8 + warp * (kTile * kTilePad);
   }
   __shared__ int s_task;
 
@@ -342,70 +272,23 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
       // ---- Phase D: fused pass over the trailing lower triangle [base, m)^2.
       const int s = m - base;
       const int nb = (s + 31) >> 5;
-      if (SMEM) {
-        for (int I = 0; I < nb; ++I) {
-          if (snake_owner(I, W) != warp) continue;
-          const int R0 = base + kTile * I;
-          double u[4] = {0.0, 0.0, 0.0, 0.0};
-          const bool ragged = R0 + kTile > m;
-          for (int J = 0; J <= I; ++J) {
-            const int C0 = base + kTile * J;
-            double* tslot = tpart + ((size_t)I * nbmax + J) * 32 + lane;
-            if (J < I && !ragged) {
-              if (upd) tile_step<SMEM, false, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
-              else     tile_step<SMEM, false, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
-            } else {
-              if (upd) tile_step<SMEM, true, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
-              else     tile_step<SMEM, true, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
-            }
-          }
-          upart[I * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
-        }
-      } else {
-        // This warp's tiles in order (its block-rows, each from J = 0 to I), with the
-        // copy of the next tile in flight while the current one is computed.
-        auto next_owned = [&](int from) {
-          int q = from;
-          while (q < nb && snake_owner(q, W) != warp) ++q;
-          return q;
-        };
-        int I = next_owned(0), J = 0, cur = 0;
-        if (I < nb) {
-          const int R0 = base + kTile * I;
-          tile_issue(S, ld, m, R0, base, lane, tile, (0 == I) || (R0 + kTile > m));
-        }
-        cp_async_commit();
+      for (int I = 0; I < nb; ++I) {
+        if (snake_owner(I, W) != warp) continue;
+        const int R0 = base + kTile * I;
         double u[4] = {0.0, 0.0, 0.0, 0.0};
-        while (I < nb) {
-          int nI = I, nJ = J + 1;
-          if (nJ > nI) { nI = next_owned(I + 1); nJ = 0; }
-          if (nI < nb) {
-            const int nR0 = base + kTile * nI;
-            tile_issue(S, ld, m, nR0, base + kTile * nJ, lane, tile + (cur ^ 1) * (kTile * kTilePad),
-                       (nJ == nI) || (nR0 + kTile > m));
-          }
-          cp_async_commit();
-          cp_async_wait1();
-          __syncwarp();
-          const int R0 = base + kTile * I, C0 = base + kTile * J;
-          double* buf = tile + cur * (kTile * kTilePad);
+        const bool ragged = R0 + kTile > m;
+        for (int J = 0; J <= I; ++J) {
+          const int C0 = base + kTile * J;
           double* tslot = tpart + ((size_t)I * nbmax + J) * 32 + lane;
-          if (J < I && R0 + kTile <= m) {
-            if (upd) tile_staged<false, true>(S, ld, m, R0, C0, lane, vP, wP, vC, buf, tslot, u);
-            else     tile_staged<false, false>(S, ld, m, R0, C0, lane, vP, wP, vC, buf, tslot, u);
+          if (J < I && !ragged) {
+            if (upd) tile_step<SMEM, false, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
+            else     tile_step<SMEM, false, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
           } else {
-            if (upd) tile_staged<true, true>(S, ld, m, R0, C0, lane, vP, wP, vC, buf, tslot, u);
-            else     tile_staged<true, false>(S, ld, m, R0, C0, lane, vP, wP, vC, buf, tslot, u);
+            if (upd) tile_step<SMEM, true, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
+            else     tile_step<SMEM, true, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
           }
-          if (J == I) {
-            upart[I * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
-            u[0] = u[1] = u[2] = u[3] = 0.0;
-          }
-          cur ^= 1;
-          I = nI;
-          J = nJ;
         }
-        cp_async_wait0();
+        upart[I * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
       }
       __syncthreads();
       // ---- Phase E: p = tau * (row partials + column partials); gamma = tau/2 p.v
@@ -465,7 +348,7 @@ size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps) {
   if (smem_path)
     d += (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 32;
   else
-    d += (size_t)warps * 2 * kTile * kTilePad;
+    d += (size_t)warps * kTile * kTilePad;
   return d * sizeof(double);
 }
 
