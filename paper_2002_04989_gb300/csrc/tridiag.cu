@@ -131,6 +131,11 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
   __syncwarp();
 }
 
+// Balanced split of the nb(nb+1)/2 lower-triangle tiles of one step over the W
+// warps (global-slot variant): warp w takes the tiles t in [start(w), start(w+1)) of
+// the row-major tile order t = I(I+1)/2 + J.
+__device__ __forceinline__ int tile_start(int w, int T, int W) { return (int)(((int64_t)w * T) / W); }
+
 __device__ __forceinline__ int snake_owner(int I, int W) {
   const int q = I / W, r = I % W;
   return (q & 1) ? (W - 1 - r) : r;
@@ -272,30 +277,68 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
       // ---- Phase D: fused pass over the trailing lower triangle [base, m)^2.
       const int s = m - base;
       const int nb = (s + 31) >> 5;
-      for (int I = 0; I < nb; ++I) {
-        if (snake_owner(I, W) != warp) continue;
-        const int R0 = base + kTile * I;
+      if (SMEM) {
+        for (int I = 0; I < nb; ++I) {
+          if (snake_owner(I, W) != warp) continue;
+          const int R0 = base + kTile * I;
+          double u[4] = {0.0, 0.0, 0.0, 0.0};
+          const bool ragged = R0 + kTile > m;
+          for (int J = 0; J <= I; ++J) {
+            const int C0 = base + kTile * J;
+            double* tslot = tpart + ((size_t)I * nbmax + J) * 32 + lane;
+            if (J < I && !ragged) {
+              if (upd) tile_step<SMEM, false, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
+              else     tile_step<SMEM, false, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
+            } else {
+              if (upd) tile_step<SMEM, true, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
+              else     tile_step<SMEM, true, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
+            }
+          }
+          upart[I * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
+        }
+      } else {
+        // contiguous, balanced range of tiles; a block-row split between warps leaves
+        // one row partial per warp (upart[(I*8 + w)*32 + l]), summed in warp order
+        const int T = nb * (nb + 1) / 2;
+        const int t0 = tile_start(warp, T, W), t1 = tile_start(warp + 1, T, W);
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= t0) ++I;
+        int J = t0 - I * (I + 1) / 2;
         double u[4] = {0.0, 0.0, 0.0, 0.0};
-        const bool ragged = R0 + kTile > m;
-        for (int J = 0; J <= I; ++J) {
-          const int C0 = base + kTile * J;
+        for (int t = t0; t < t1; ++t) {
+          const int R0 = base + kTile * I, C0 = base + kTile * J;
           double* tslot = tpart + ((size_t)I * nbmax + J) * 32 + lane;
-          if (J < I && !ragged) {
+          if (J < I && R0 + kTile <= m) {
             if (upd) tile_step<SMEM, false, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
             else     tile_step<SMEM, false, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
           } else {
             if (upd) tile_step<SMEM, true, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
             else     tile_step<SMEM, true, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
           }
+          if (J == I || t == t1 - 1) {
+            upart[((size_t)I * 8 + warp) * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
+            u[0] = u[1] = u[2] = u[3] = 0.0;
+          }
+          if (++J > I) { ++I; J = 0; }
         }
-        upart[I * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
       }
       __syncthreads();
       // ---- Phase E: p = tau * (row partials + column partials); gamma = tau/2 p.v
       double dot = 0.0;
       for (int i = base + tid; i < m; i += NT) {
         const int r = i - base, I = r >> 5, l = r & 31;
-        double p = upart[I * 32 + l];
+        double p;
+        if (SMEM) {
+          p = upart[I * 32 + l];
+        } else {
+          // warps whose tile ranges meet block-row I, in warp order
+          const int T = nb * (nb + 1) / 2, ta = I * (I + 1) / 2, tb = ta + I;
+          p = 0.0;
+          for (int w = 0; w < W; ++w) {
+            const int s0 = tile_start(w, T, W), s1 = tile_start(w + 1, T, W);
+            if (s0 < s1 && s0 <= tb && s1 > ta) p += upart[((size_t)I * 8 + w) * 32 + l];
+          }
+        }
         for (int I2 = I; I2 < nb; ++I2) p += tpart[((size_t)I2 * nbmax + I) * 32 + l];
         p *= tau;
         wC[i] = p;
@@ -339,7 +382,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
 
 size_t tridiag_global_slot_doubles(int max_m) {
   const Layout L = make_layout(false, max_m);
-  return (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 32 + 32;
+  return (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 8 * 32 + 32;
 }
 
 size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps) {
