@@ -106,7 +106,7 @@ TriCfg tri_cfg_default(int m) {
   if (m <= 32) return {true, 1};
   if (m <= 64) return {true, 2};
   if (m <= kTridiagSmemMaxM) return {true, 4};
-  if (m <= 2048) return {false, 4};
+  if (m <= 512) return {false, 4};
   return {false, 8};
 }
 inline int cfg_key(const TriCfg& c) { return (c.smem ? 0 : 16) + c.warps; }

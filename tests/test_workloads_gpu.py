@@ -1,0 +1,94 @@
+"""Parity at the full sizes of the other workloads, in the launch configuration the
+benchmark times: the n = 4096 planted matrix with 256 seeded columns (all of its
+1,048,576 components against the closed form Q o Q, sampled minors against the
+secular roots) and the 4096-matrix uneven batch in one batched call (sampled
+matrices against the long-double oracle, every matrix against the invariants)."""
+import numpy as np
+import pytest
+
+from invariants import grid_errors, spectrum_errors
+from paper_2002_04989_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_VSQ = 1e-10
+TOL_LAM_REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    from paper_2002_04989_gb300 import eeid
+    c = eeid.Context(0)
+    yield c
+    c.close()
+
+
+def test_planted4096_selected_columns(torch_cuda, ctx, oracle_mod):
+    torch = torch_cuda
+    p, cols = inputs.planted4096()
+    A = torch.from_numpy(p.A).cuda()
+    lam = torch.empty(4096, dtype=torch.float64, device="cuda")
+    out = ctx.eeid_components(A, cols=cols, lam=lam).cpu().numpy()
+    st = ctx.eeid_sync()
+    assert st in (0, 2)          # the min gap 1e-4 on [-10, 10] is 1e-5 relative: warning 2
+    ref = (p.Q * p.Q).T[:, cols]
+    err = np.max(np.abs(out - ref))
+    lam_h = lam.cpu().numpy()
+    print(f"planted4096: max|d vsq| = {err:.3e}, max|d lam| = {np.max(np.abs(lam_h - p.lam)):.3e}")
+    assert err <= TOL_VSQ
+    assert np.max(np.abs(lam_h - p.lam)) <= TOL_LAM_REL * 10.0
+    assert grid_errors(p.A, lam_h, out, cols)["col_sum"] < 1e-10
+    sample = cols[[0, 128, 255]]
+    mu = ctx.eeid_minor_eigvals(A, cols=sample).cpu().numpy()
+    ctx.eeid_sync()
+    mu_ref = oracle_mod.secular_minor_eigvals(p.lam, p.Q, sample)
+    assert np.max(np.abs(mu - mu_ref)) <= TOL_LAM_REL * 10.0
+
+
+def test_batch4096_one_batched_call(torch_cuda, ctx, oracle_mod):
+    torch = torch_cuda
+    mats = inputs.batch4096()
+    probs = []
+    for A in mats:
+        n = A.shape[0]
+        probs.append({"A": torch.from_numpy(A).cuda(),
+                      "out": torch.empty((n, n), dtype=torch.float64, device="cuda"),
+                      "lam": torch.empty(n, dtype=torch.float64, device="cuda")})
+    ctx.eeid_components_batched(probs)
+    ctx.eeid_sync()
+    # every matrix: invariants of an orthonormal eigenbasis (bars scaled to its size)
+    worst = 0.0
+    for A, pr in zip(mats, probs):
+        out, lam = pr["out"].cpu().numpy(), pr["lam"].cpu().numpy()
+        g = grid_errors(A, lam, out)
+        s = spectrum_errors(A, lam)
+        norm = max(abs(lam[0]), abs(lam[-1]), 1e-300)
+        if inputs.min_relative_gap(lam) >= 1e-4:
+            worst = max(worst, g["col_sum"], g["row_sum"])
+            assert g["col_sum"] < 1e-9 and g["row_sum"] < 1e-9
+        assert s["trace"] <= 1e-12 * norm * A.shape[0] and s["sorted"] == 0
+    print(f"batch4096: worst row/col-sum deviation (gap clause met) = {worst:.3e}")
+    # sampled matrices against the oracle (small ones in full, larger on sampled rows/cols)
+    rng = np.random.default_rng(0)
+    for idx in rng.choice(len(mats), 10, replace=False):
+        A = mats[idx]
+        n = A.shape[0]
+        out = probs[idx]["out"].cpu().numpy()
+        if n <= 64:
+            ref, lam_ref, _ = oracle_mod.components(A, method=0, want_eigs=True)
+            got = out
+        else:
+            rows = np.unique(np.r_[0, n - 1, rng.choice(n, 3, replace=False)])
+            cols = np.unique(np.r_[0, n - 1, rng.choice(n, 2, replace=False)])
+            ref, lam_ref, _ = oracle_mod.components(A, rows=rows, cols=cols, method=0, want_eigs=True)
+            got = out[np.ix_(rows, cols)]
+        bar = TOL_VSQ if inputs.min_relative_gap(lam_ref) >= 1e-4 else 1e-6
+        assert np.max(np.abs(got - ref)) <= bar, (idx, n)
