@@ -76,9 +76,11 @@ def test_batch4096_one_batched_call(torch_cuda, ctx, oracle_mod):
             assert g["col_sum"] < 1e-9 and g["row_sum"] < 1e-9
         assert s["trace"] <= 1e-12 * norm * A.shape[0] and s["sorted"] == 0
     print(f"batch4096: worst row/col-sum deviation (gap clause met) = {worst:.3e}")
-    # sampled matrices against the oracle (small ones in full, larger on sampled rows/cols)
+    # sampled matrices (n <= 128, so the long-double oracle stays within seconds) against
+    # the oracle: n <= 64 in full, larger ones on sampled rows and columns
     rng = np.random.default_rng(0)
-    for idx in rng.choice(len(mats), 10, replace=False):
+    small = [i for i, A in enumerate(mats) if A.shape[0] <= 128]   # oracle cost bound
+    for idx in rng.choice(small, 10, replace=False):
         A = mats[idx]
         n = A.shape[0]
         out = probs[idx]["out"].cpu().numpy()
