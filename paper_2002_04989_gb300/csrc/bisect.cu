@@ -27,6 +27,13 @@
 //  * (d_i, e_{i-1}^2) are staged in shared memory as one 16-byte pair per step and
 //    read as a warp-wide broadcast; each warp loops until a warp vote finds every
 //    lane converged.
+//  * Two phases.  FP32 runs at ~60x the FP64 rate on this part, so the bracket is
+//    first narrowed to ~2^-41 ||T|| with Sturm counts in double-float arithmetic
+//    (pairs of FP32 values, ~2^-44 relative per operation).  The FP64 phase then
+//    widens that bracket by 2^-40 ||T||, re-verifies it with two exact-FP64 Sturm
+//    counts and finishes the bisection in FP64.  A bracket that fails the check
+//    (the cheap phase misjudged, or the interlacing seed was wrong) falls back to
+//    the Gershgorin bracket, so the result never depends on the FP32 phase.
 #include "internal.cuh"
 
 namespace eeid {
@@ -72,6 +79,86 @@ __device__ __forceinline__ int sturm_count(const double2* __restrict__ de, int m
         pn *= f;
         pc *= f;
         hn = hi_of(pn);
+      }
+    }
+    cnt += ((hn ^ hc) >> 31) & 1;
+    pm = pc;
+    pc = pn;
+    hc = hn;
+  }
+  return cnt;
+}
+
+// ---- double-float arithmetic: a value is hi + lo with two FP32 numbers, built from
+// the error-free transformations of Dekker (1971) and Knuth (TAOCP vol. 2, 4.2.2):
+// two_sum and two_prod return a rounded result and its exact rounding error.
+struct dflt {
+  float h, l;
+};
+__device__ __forceinline__ dflt df_quick(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b.h - bb) + (a.l + b.l);
+  return df_quick(s, e);
+}
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ dflt df_of(double v) {   // round to the nearest double-float
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double df_val(dflt a) { return (double)a.h + (double)a.l; }
+
+constexpr int kTinyF = 127 - 100;  // 2^-100 as an FP32 biased exponent
+
+// Number of eigenvalues below x of the scaled tridiagonal, with the three-term
+// recurrence evaluated in double-float (q[i] = (d_i hi, d_i lo, e_{i-1}^2 hi, lo)).
+// Same conventions as the FP64 count; the pair is rescaled by powers of two to keep
+// its larger exponent in [2^-40, 2^40] (FP32 range).
+__device__ __forceinline__ int sturm_count_df(const float4* __restrict__ q, int m, dflt x) {
+  const dflt nx = {-x.h, -x.l};
+  dflt pm = {1.0f, 0.0f};
+  float4 q0 = q[0];
+  dflt pc = df_add({q0.x, q0.y}, nx);
+  int hc = __float_as_int(pc.h);
+  if (((hc >> 23) & 0xff) == 0) {
+    const int sgn = ((hc & 0x7fffffff) == 0) ? int(0x80000000u) : (hc & int(0x80000000u));
+    pc = {__int_as_float(sgn | (kTinyF << 23)), 0.0f};
+    hc = __float_as_int(pc.h);
+  }
+  int cnt = (hc >> 31) & 1;
+  for (int i = 1; i < m; ++i) {
+    const float4 qi = q[i];
+    const dflt t = df_add({qi.x, qi.y}, nx);
+    const dflt a = df_mul(t, pc);
+    const dflt b = df_mul({qi.z, qi.w}, pm);
+    dflt pn = df_add(a, {-b.h, -b.l});
+    int hn = __float_as_int(pn.h);
+    int en = (hn >> 23) & 0xff;
+    const int ec = (hc >> 23) & 0xff;
+    if (en == 0 || (unsigned)(max(en, ec) - (127 - 40)) > 80u) {
+      if (en == 0) {
+        const bool zero = (hn & 0x7fffffff) == 0;
+        const int sgn = zero ? ((~hc) & int(0x80000000u)) : (hn & int(0x80000000u));
+        pn = {__int_as_float(sgn | (kTinyF << 23)), 0.0f};
+        hn = __float_as_int(pn.h);
+        en = (hn >> 23) & 0xff;
+      }
+      const int em = max(en, ec);
+      if ((unsigned)(em - (127 - 40)) > 80u) {
+        const float f = __int_as_float((254 - em) << 23);  // 2^(127 - em)
+        pn.h *= f; pn.l *= f;
+        pc.h *= f; pc.l *= f;
+        hn = __float_as_int(pn.h);
       }
     }
     cnt += ((hn ^ hc) >> 31) & 1;
@@ -130,10 +217,14 @@ k_bisect(const BisectTask* __restrict__ tasks, const BisectItem* __restrict__ it
   frexp(tn, &ex);                   // tn * 2^-ex in [0.5, 1)
   const double sc = ldexp(1.0, -ex);
   const double isc = ldexp(1.0, ex);
+  float4* dq = (float4*)(de + m);   // double-float copy of the table
   for (int i = tid; i < m; i += blockDim.x) {
     const double d = T.d[i] * sc;
     const double e = (i > 0) ? T.e[i - 1] * sc : 0.0;
-    de[i] = make_double2(d, e * e);
+    const double e2 = e * e;
+    de[i] = make_double2(d, e2);
+    const dflt dd = df_of(d), ee = df_of(e2);
+    dq[i] = make_float4(dd.h, dd.l, ee.h, ee.l);
   }
   __syncthreads();
 
@@ -147,8 +238,29 @@ k_bisect(const BisectTask* __restrict__ tasks, const BisectItem* __restrict__ it
     lo = fmax(lo, glo);
     hi = fmin(hi, ghi);
   }
-  // Verify interlacing brackets (count(lo) <= k < count(hi)); fall back if not.
-  if (T.parent != nullptr) {
+  // Phase 1 (double-float): bisect until the bracket is below 2^-41 of the scale.
+  {
+    dflt dlo = df_of(lo), dhi = df_of(hi);
+    bool act = active;
+    int it1 = 0;
+    while (__any_sync(0xffffffffu, act)) {
+      if (act) {
+        dflt mid = df_add(dlo, dhi);
+        mid.h *= 0.5f;
+        mid.l *= 0.5f;
+        if (sturm_count_df(dq, m, mid) > k) dhi = mid; else dlo = mid;
+        const dflt w = df_add(dhi, {-dlo.h, -dlo.l});
+        act = (w.h > 0x1p-41f) && (++it1 < 64);
+      }
+    }
+    if (active) {
+      lo = fmax(df_val(dlo) - 0x1p-40, glo);
+      hi = fmin(df_val(dhi) + 0x1p-40, ghi);
+    }
+  }
+  // Phase 2 (FP64): verify the narrowed bracket (count(lo) <= k < count(hi)) with
+  // exact FP64 counts; fall back to the Gershgorin bracket if it fails.
+  {
     bool fell = false;
     if (active) {
       if (sturm_count(de, m, lo) > k) { lo = glo; fell = true; }
@@ -173,7 +285,7 @@ k_bisect(const BisectTask* __restrict__ tasks, const BisectItem* __restrict__ it
 cudaError_t launch_bisect(const BisectTask* tasks, const BisectItem* items, int nitems, int max_m,
                           unsigned* status, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  const size_t smem = (size_t)max_m * sizeof(double2);
+  const size_t smem = (size_t)max_m * (sizeof(double2) + sizeof(float4));
   cudaError_t e = cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
