@@ -544,7 +544,7 @@ def run_profile_case(case: str) -> int:
     from paper_2002_04989_gb300 import eeid, inputs
     p = inputs.planted1024()
     A = torch.from_numpy(p.A).cuda()
-    cols = np.arange(151)
+    cols = np.arange(151 if case == "tridiag152" else 303)
     ctx = eeid.Context(0)
     for _ in range(2):
         out = ctx.eeid_components(A, cols=cols)
@@ -571,10 +571,10 @@ def main(argv=None):
                     help="serving: length of the prefix of the seeded request stream")
     ap.add_argument("--serving-rates", default="0.5,1,2",
                     help="serving: comma-separated Poisson arrival rates (requests/s)")
-    ap.add_argument("--profile-case", choices=("tridiag152",), default=None,
-                    help="run only a small case for an ncu capture and exit: tridiag152 = "
-                         "A plus the minors M_0..M_150 of the planted n=1024 matrix (one "
-                         "CTA per SM), called twice")
+    ap.add_argument("--profile-case", choices=("tridiag152", "tridiag304"), default=None,
+                    help="run only a small case for an ncu capture and exit: tridiag152 / "
+                         "tridiag304 = A plus the first 151 / 303 minors of the planted "
+                         "n=1024 matrix (one / two CTAs per SM), called twice")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)   # timing rule: at least 3 untimed warm-up steps
     world, rank, local = dist_env()
