@@ -69,8 +69,8 @@ struct eeid_ctx {
   cudaEvent_t stage_ev = nullptr;
   bool stage_used = false;
   int64_t launches = 0;
-  int occ_cache[2][9] = {};  // blocks/SM per (smem path, warps) at the last max_m
-  int occ_m[2][9] = {};
+  int occ_cache[2][17] = {};  // blocks/SM per (smem path, warps) at the last max_m
+  int occ_m[2][17] = {};
   struct Rule { int lo, hi; bool smem; int warps; };
   std::vector<Rule> rules;  // tuning overrides, later ones win
   int rules_version = 0;
@@ -109,11 +109,11 @@ TriCfg tri_cfg_default(int m) {
   if (m <= 512) return {false, 4};
   return {false, 8};
 }
-inline int cfg_key(const TriCfg& c) { return (c.smem ? 0 : 16) + c.warps; }
+inline int cfg_key(const TriCfg& c) { return (c.smem ? 0 : 32) + c.warps; }
 
 bool cfg_supported(bool smem, int warps, int m) {
   if (smem) return (warps == 1 || warps == 2 || warps == 4 || warps == 8) && m <= kTridiagSmemMaxM;
-  return (warps == 2 || warps == 4 || warps == 8) && m <= kTridiagMaxM;
+  return (warps == 2 || warps == 4 || warps == 8 || warps == 16) && m <= kTridiagMaxM;
 }
 
 struct Problem {
@@ -311,12 +311,12 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     }
   }
   // tridiagonalisation groups (one persistent launch per configuration)
-  std::vector<std::vector<int>> groups(32);
+  std::vector<std::vector<int>> groups(64);
   for (size_t t = 0; t < tri.size(); ++t) groups[cfg_key(tri_cfg(ctx, tri[t].m))].push_back((int)t);
   struct GroupPlan { TriCfg cfg; int max_m; int grid; size_t task_off, counter_off, work_off;
                      size_t slot; std::vector<int> idx; };
   std::vector<GroupPlan> gplans;
-  for (int key = 0; key < 32; ++key) {
+  for (int key = 0; key < 64; ++key) {
     if (groups[key].empty()) continue;
     GroupPlan g;
     g.idx = groups[key];
@@ -666,7 +666,7 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
     struct Cand { TriCfg c; int grid; size_t slot; };
     std::vector<Cand> cands;
     for (int path = 0; path < 2; ++path)
-      for (int w : {1, 2, 4, 8}) {
+      for (int w : {1, 2, 4, 8, 16}) {
         if (!cfg_supported(path == 0, w, m)) continue;
         TriCfg c{path == 0, w};
         const int grid = (int)std::min<int64_t>(T, (int64_t)ctx->sms * blocks_per_sm(ctx, c, m));

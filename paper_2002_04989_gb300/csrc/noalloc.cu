@@ -24,12 +24,12 @@ using namespace eeid;
 namespace {
 
 // Largest n accepted.  The working matrix and its tile partial sums take
-// n*round4(n) + nb^2*32 + nb*8*32 + 32 doubles (nb = ceil(n/32)); at n = 512 that is
-// 274,464 doubles.
+// n*round4(n) + nb^2*32 + nb*16*32 + 32 doubles (nb = ceil(n/32)); at n = 512 that is
+// 278,560 doubles.
 constexpr int kNoAllocMaxN = 512;
 constexpr int kNoAllocWarps = 4;
 constexpr size_t kNb = (kNoAllocMaxN + 31) / 32;
-constexpr size_t kSlotDoubles = (size_t)kNoAllocMaxN * kNoAllocMaxN + kNb * kNb * 32 + kNb * 8 * 32 + 32;
+constexpr size_t kSlotDoubles = (size_t)kNoAllocMaxN * kNoAllocMaxN + kNb * kNb * 32 + kNb * 16 * 32 + 32;
 constexpr size_t kDEDoubles = 2 * (size_t)kNoAllocMaxN;         // d[n], e[n-1]
 constexpr size_t kMetaDoubles = 64;                              // 512 bytes of descriptors
 constexpr size_t kScratchDoubles = kSlotDoubles + kDEDoubles + kMetaDoubles;

@@ -158,7 +158,7 @@ __host__ __device__ inline Layout make_layout(bool smem, int max_m) {
 // Minimum resident CTAs per SM the register allocation must allow.
 template <bool SMEM, int W>
 struct MinBlocks {
-  static constexpr int value = (W >= 8) ? 2 : (SMEM && W <= 2) ? 8 : 4;
+  static constexpr int value = (W >= 16) ? 1 : (W >= 8) ? 2 : (SMEM && W <= 2) ? 8 : 4;
 };
 
 template <bool SMEM, int W>
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
         }
       } else {
         // contiguous, balanced range of tiles; a block-row split between warps leaves
-        // one row partial per warp (upart[(I*8 + w)*32 + l]), summed in warp order
+        // one row partial per warp (upart[(I*16 + w)*32 + l]), summed in warp order
         const int T = nb * (nb + 1) / 2;
         const int t0 = tile_start(warp, T, W), t1 = tile_start(warp + 1, T, W);
         int I = 0;
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
             else     tile_step<SMEM, true, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
           }
           if (J == I || t == t1 - 1) {
-            upart[((size_t)I * 8 + warp) * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
+            upart[((size_t)I * 16 + warp) * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
             u[0] = u[1] = u[2] = u[3] = 0.0;
           }
           if (++J > I) { ++I; J = 0; }
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
           p = 0.0;
           for (int w = 0; w < W; ++w) {
             const int s0 = tile_start(w, T, W), s1 = tile_start(w + 1, T, W);
-            if (s0 < s1 && s0 <= tb && s1 > ta) p += upart[((size_t)I * 8 + w) * 32 + l];
+            if (s0 < s1 && s0 <= tb && s1 > ta) p += upart[((size_t)I * 16 + w) * 32 + l];
           }
         }
         for (int I2 = I; I2 < nb; ++I2) p += tpart[((size_t)I2 * nbmax + I) * 32 + l];
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
 
 size_t tridiag_global_slot_doubles(int max_m) {
   const Layout L = make_layout(false, max_m);
-  return (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 8 * 32 + 32;
+  return (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 16 * 32 + 32;
 }
 
 size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps) {
@@ -419,6 +419,7 @@ cudaError_t launch_tridiag(bool smem_path, int warps, int grid, const TridiagLau
       case 2: return launch_one<false, 2>(grid, L, s);
       case 4: return launch_one<false, 4>(grid, L, s);
       case 8: return launch_one<false, 8>(grid, L, s);
+      case 16: return launch_one<false, 16>(grid, L, s);
     }
   }
   return cudaErrorInvalidValue;
@@ -436,7 +437,7 @@ int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tridiag<S_, W_>, W_ * 32, smem); \
   }
   EEID_OCC(true, 1) EEID_OCC(true, 2) EEID_OCC(true, 4) EEID_OCC(true, 8)
-  EEID_OCC(false, 2) EEID_OCC(false, 4) EEID_OCC(false, 8)
+  EEID_OCC(false, 2) EEID_OCC(false, 4) EEID_OCC(false, 8) EEID_OCC(false, 16)
 #undef EEID_OCC
   return e == cudaSuccess ? nb : 0;
 }
