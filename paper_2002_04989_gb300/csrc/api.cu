@@ -102,18 +102,23 @@ struct TriCfg {
   bool smem;
   int warps;
 };
+constexpr size_t kMaxSmemPerBlock = 232448;  // opt-in shared memory per CTA on sm_103a
+
 TriCfg tri_cfg_default(int m) {
   if (m <= 32) return {true, 1};
   if (m <= 64) return {true, 2};
   if (m <= kTridiagSmemMaxM) return {true, 4};
   if (m <= 512) return {false, 4};
+  if (tridiag_smem_bytes(false, m, 16) <= kMaxSmemPerBlock) return {false, 16};
   return {false, 8};
 }
 inline int cfg_key(const TriCfg& c) { return (c.smem ? 0 : 32) + c.warps; }
 
 bool cfg_supported(bool smem, int warps, int m) {
-  if (smem) return (warps == 1 || warps == 2 || warps == 4 || warps == 8) && m <= kTridiagSmemMaxM;
-  return (warps == 2 || warps == 4 || warps == 8 || warps == 16) && m <= kTridiagMaxM;
+  bool ok;
+  if (smem) ok = (warps == 1 || warps == 2 || warps == 4 || warps == 8) && m <= kTridiagSmemMaxM;
+  else ok = (warps == 2 || warps == 4 || warps == 8 || warps == 16) && m <= kTridiagMaxM;
+  return ok && tridiag_smem_bytes(smem, m, warps) <= kMaxSmemPerBlock;
 }
 
 struct Problem {
