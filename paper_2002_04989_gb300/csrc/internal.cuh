@@ -63,7 +63,7 @@ struct BisectItem {
   int task;
   int k0;
 };
-constexpr int kBisectThreads = 128;
+constexpr int kBisectThreads = 256;
 cudaError_t launch_bisect(const BisectTask* tasks, const BisectItem* items, int nitems,
                           int max_m, unsigned* status, cudaStream_t s);
 

@@ -38,7 +38,7 @@ constexpr size_t kScratchDoubles = kSlotDoubles + kDEDoubles + kMetaDoubles;
 constexpr size_t kOffTask = 0;       // TridiagTask
 constexpr size_t kOffCounter = 64;   // int work counter (must start at 0)
 constexpr size_t kOffBisect = 128;   // BisectTask
-constexpr size_t kOffItems = 192;    // BisectItem[ceil(n/128)] (<= 4 items)
+constexpr size_t kOffItems = 192;    // BisectItem[ceil(n/kBisectThreads)] (<= 4 items)
 constexpr size_t kOffStatus = 256;   // unsigned status word
 static_assert(sizeof(TridiagTask) <= 64, "descriptor layout");
 static_assert(sizeof(BisectTask) <= 64, "descriptor layout");
