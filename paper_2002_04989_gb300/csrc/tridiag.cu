@@ -79,16 +79,20 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
   const int c = C0 + lane;
   const bool cv = !EDGE || c < m;
   const double vPc = UPD ? vP[c] : 0.0, wPc = UPD ? wP[c] : 0.0;
+  // rows of this tile inside the matrix: a warp-uniform bound, so a ragged tile
+  // issues no FP64 instructions for the rows past m (full 16-row slabs unrolled,
+  // the remaining rows one at a time)
+  const int nrows = EDGE ? min(T, m - R0) : T;
   double t0 = 0.0, t1 = 0.0;
-  // column half in two 16-row slabs (bounded register use)
+  int h = 0;
 #pragma unroll 1
-  for (int h = 0; h < T; h += 16) {
+  for (; h + 16 <= nrows; h += 16) {
     double a[16];
     const double* src = S + (size_t)(R0 + h) * ld + c;
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr) {
       const int i = R0 + h + rr;
-      const bool ok = !EDGE || (cv && i < m && i >= c);
+      const bool ok = !EDGE || (cv && i >= c);
       a[rr] = ok ? src[(size_t)rr * ld] : 0.0;
     }
     if (UPD) {
@@ -97,7 +101,7 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
       for (int rr = 0; rr < 16; ++rr) {
         const int i = R0 + h + rr;
         const double x = fma(-vP[i], wPc, fma(-wP[i], vPc, a[rr]));
-        const bool ok = !EDGE || (cv && i < m && i >= c);
+        const bool ok = !EDGE || (cv && i >= c);
         a[rr] = ok ? x : 0.0;
         if (ok) dst[(size_t)rr * ld] = a[rr];
       }
@@ -114,6 +118,20 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
     if (!SMEM) {
 #pragma unroll
       for (int rr = 0; rr < 16; ++rr) tile[(h + rr) * TP + lane] = a[rr];
+    }
+  }
+  if (EDGE) {
+    for (int rr = h; rr < nrows; ++rr) {
+      const int i = R0 + rr;
+      const bool ok = cv && i >= c;
+      double a = ok ? S[(size_t)i * ld + c] : 0.0;
+      if (UPD) {
+        const double x = fma(-vP[i], wPc, fma(-wP[i], vPc, a));
+        a = ok ? x : 0.0;
+        if (ok) S[(size_t)i * ld + c] = a;
+      }
+      t0 = fma((i > c) ? a : 0.0, vC[i], t0);
+      if (!SMEM) tile[rr * TP + lane] = a;
     }
   }
   *tslot = t0 + t1;
