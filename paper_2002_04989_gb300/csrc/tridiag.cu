@@ -149,6 +149,62 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
   __syncwarp();
 }
 
+// Diagonal tile (global-slot variant): its lower triangle holds 528 of 1024 slots, so
+// the lane-per-column mapping of tile_step would issue every FP64 instruction with half
+// the lanes masked.  Here the update is packed: warp-row r < 15 holds row r (lanes
+// 0..r) and row 30-r (lanes r+1..31), then row 15 and row 31, 17 warp-rows in all.  The
+// updated values are mirrored into the shared tile, and one unmasked pass over the
+// full symmetric tile gives both halves of the product (row partials only; the tile's
+// column partial is 0).  FP64 issue: 2 x 17 + 32 = 66 instructions instead of 128.
+template <bool UPD>
+__device__ __forceinline__ void diag_tile(double* S, int64_t ld, int m, int R0, int lane,
+                                          const double* vP, const double* wP, const double* vC,
+                                          double* tile, double* tslot, double (&u)[4]) {
+  constexpr int TP = 33;
+  const int nrows = min(32, m - R0);   // rows (= columns) of the tile inside the matrix
+#pragma unroll
+  for (int it = 0; it < 17; ++it) {
+    int i, c;
+    bool valid;
+    if (it < 15) {
+      const bool first = lane <= it;
+      i = first ? it : 30 - it;
+      c = first ? lane : lane - it - 1;
+      valid = true;
+    } else if (it == 15) {
+      i = 15;
+      c = lane;
+      valid = lane <= 15;
+    } else {
+      i = 31;
+      c = lane;
+      valid = true;
+    }
+    valid = valid && i < nrows;
+    double* ptr = S + (size_t)(R0 + i) * ld + (R0 + c);
+    double a = valid ? *ptr : 0.0;
+    if (UPD) {
+      const double x = fma(-vP[R0 + i], wP[R0 + c], fma(-wP[R0 + i], vP[R0 + c], a));
+      a = valid ? x : 0.0;
+      if (valid) *ptr = a;
+    }
+    if (valid) {
+      tile[i * TP + c] = a;
+      tile[c * TP + i] = a;
+    }
+  }
+  *tslot = 0.0;
+  __syncwarp();
+  const int i = lane;
+#pragma unroll
+  for (int cc = 0; cc < 32; ++cc) {
+    const bool ok = i < nrows && cc < nrows;
+    const double x = ok ? tile[i * TP + cc] : 0.0;
+    u[cc & 3] = fma(x, vC[R0 + cc], u[cc & 3]);
+  }
+  __syncwarp();
+}
+
 // Balanced split of the nb(nb+1)/2 lower-triangle tiles of one step over the W
 // warps (global-slot variant): warp w takes the tiles t in [start(w), start(w+1)) of
 // the row-major tile order t = I(I+1)/2 + J.
@@ -329,6 +385,9 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
           if (J < I && R0 + kTile <= m) {
             if (upd) tile_step<SMEM, false, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
             else     tile_step<SMEM, false, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
+          } else if (J == I) {
+            if (upd) diag_tile<true>(S, ld, m, R0, lane, vP, wP, vC, tile, tslot, u);
+            else     diag_tile<false>(S, ld, m, R0, lane, vP, wP, vC, tile, tslot, u);
           } else {
             if (upd) tile_step<SMEM, true, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
             else     tile_step<SMEM, true, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
