@@ -148,7 +148,7 @@ int64_t eeid_launch_count(const eeid_ctx* ctx);
 /* Tuning of the Householder kernel (K-a): matrices of size m in [m_lo, m_hi] are
  * reduced by the variant `path` (0 = working matrix resident in shared memory,
  * m <= 160; 1 = working matrix in a global-memory slot per CTA) with `warps` warps
- * per CTA (path 0: 1, 2, 4, 8; path 1: 2, 4, 8, 16).  Later rules take precedence.
+ * per CTA (path 0: 1, 2, 4, 8; path 1: 2, 4, 8, 12, 16).  Later rules take precedence.
  * Results are bitwise reproducible for a fixed rule set; changing the variant of a
  * size changes the rounding order (not the accuracy class).  EEID_ERR_INVALID for
  * an unsupported combination. */

@@ -110,6 +110,7 @@ TriCfg tri_cfg_default(int m) {
   if (m <= kTridiagSmemMaxM) return {true, 4};
   if (m <= 512) return {false, 4};
   if (tridiag_smem_bytes(false, m, 16) <= kMaxSmemPerBlock) return {false, 16};
+  if (tridiag_smem_bytes(false, m, 12) <= kMaxSmemPerBlock) return {false, 12};
   return {false, 8};
 }
 inline int cfg_key(const TriCfg& c) { return (c.smem ? 0 : 32) + c.warps; }
@@ -117,7 +118,7 @@ inline int cfg_key(const TriCfg& c) { return (c.smem ? 0 : 32) + c.warps; }
 bool cfg_supported(bool smem, int warps, int m) {
   bool ok;
   if (smem) ok = (warps == 1 || warps == 2 || warps == 4 || warps == 8) && m <= kTridiagSmemMaxM;
-  else ok = (warps == 2 || warps == 4 || warps == 8 || warps == 16) && m <= kTridiagMaxM;
+  else ok = (warps == 2 || warps == 4 || warps == 8 || warps == 12 || warps == 16) && m <= kTridiagMaxM;
   return ok && tridiag_smem_bytes(smem, m, warps) <= kMaxSmemPerBlock;
 }
 

@@ -232,7 +232,7 @@ __host__ __device__ inline Layout make_layout(bool smem, int max_m) {
 // Minimum resident CTAs per SM the register allocation must allow.
 template <bool SMEM, int W>
 struct MinBlocks {
-  static constexpr int value = (W >= 16) ? 1 : (W >= 8) ? 2 : (SMEM && W <= 2) ? 8 : 4;
+  static constexpr int value = (W >= 12) ? 1 : (W >= 8) ? 2 : (SMEM && W <= 2) ? 8 : 4;
 };
 
 template <bool SMEM, int W>
@@ -244,11 +244,14 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
   const int64_t ld = Ly.ld;
   const int nbmax = Ly.nbmax;
 
+  // Three vectors: v of the previous step (vP), v of this step (vC), and w.  The
+  // fused pass reads the previous w; once it is done that w is dead, so this step's
+  // w (first p) is written into the same buffer (wC aliases wP).
   double* vP = sm;
   double* wP = vP + Ly.VM;
   double* vC = wP + Ly.VM;
-  double* wC = vC + Ly.VM;
-  double* red = wC + Ly.VM;       // W*32 + 1 reduction slots (+ padding)
+  double* const wC = wP;
+  double* red = vC + Ly.VM;       // W*32 + 1 reduction slots (+ padding)
   double* scal = red + W * 32 + 8;  // 8 scalars
   double* S;
   double* tpart;
@@ -284,13 +287,12 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
     double* __restrict__ eout = task.e;
 
     // Edge tiles multiply zeros by vector entries past m; those entries must be
-    // finite, so the tails [m, VM) of all four vectors are cleared per task (shared
+    // finite, so the tails [m, VM) of the three vectors are cleared per task (shared
     // memory keeps whatever an earlier task or launch left there).
     for (int i = m + tid; i < Ly.VM; i += NT) {
       vP[i] = 0.0;
       wP[i] = 0.0;
       vC[i] = 0.0;
-      wC[i] = 0.0;
     }
 
     // a1: the minor view -- copy the lower triangle of A without row/col `skip`.
@@ -429,7 +431,6 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
       }
       __syncthreads();
       double* tv = vP; vP = vC; vC = tv;
-      double* tw = wP; wP = wC; wC = tw;
     }
     // Last 2x2 block (or 1x1): apply the final update and read off d, e.
     if (tid == 0) {
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
     }
     __syncthreads();
     // restore the canonical vector order for the next task (pointer swaps above)
-    vP = sm; wP = vP + Ly.VM; vC = wP + Ly.VM; wC = vC + Ly.VM;
+    vP = sm; vC = sm + 2 * (size_t)Ly.VM;
   }
 }
 
@@ -464,7 +465,7 @@ size_t tridiag_global_slot_doubles(int max_m) {
 
 size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps) {
   const Layout L = make_layout(smem_path, max_m);
-  size_t d = 4 * (size_t)L.VM + (size_t)warps * 32 + 8 + 8;
+  size_t d = 3 * (size_t)L.VM + (size_t)warps * 32 + 8 + 8;
   if (smem_path)
     d += (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 32;
   else
@@ -496,6 +497,7 @@ cudaError_t launch_tridiag(bool smem_path, int warps, int grid, const TridiagLau
       case 2: return launch_one<false, 2>(grid, L, s);
       case 4: return launch_one<false, 4>(grid, L, s);
       case 8: return launch_one<false, 8>(grid, L, s);
+      case 12: return launch_one<false, 12>(grid, L, s);
       case 16: return launch_one<false, 16>(grid, L, s);
     }
   }
@@ -514,7 +516,7 @@ int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tridiag<S_, W_>, W_ * 32, smem); \
   }
   EEID_OCC(true, 1) EEID_OCC(true, 2) EEID_OCC(true, 4) EEID_OCC(true, 8)
-  EEID_OCC(false, 2) EEID_OCC(false, 4) EEID_OCC(false, 8) EEID_OCC(false, 16)
+  EEID_OCC(false, 2) EEID_OCC(false, 4) EEID_OCC(false, 8) EEID_OCC(false, 12) EEID_OCC(false, 16)
 #undef EEID_OCC
   return e == cudaSuccess ? nb : 0;
 }
