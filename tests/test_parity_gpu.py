@@ -338,3 +338,71 @@ def test_phase_times_with_graphs(torch_cuda, ctx):
     finally:
         ctx.eeid_set_timing(False)
     ctx.eeid_sync()
+
+
+def test_every_output_written_poisoned_buffers(torch_cuda, ctx):
+    """Outputs pre-filled with NaN come back fully written (no entry skipped), for the
+    grid, the eigenvalues and the minor eigenvalues, across tile-boundary sizes."""
+    torch = torch_cuda
+    for n in (31, 33, 161, 300):
+        A = dev(torch, inputs.goe(n, 90 + n))
+        out = torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda")
+        lam = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        ctx.eeid_components(A, out=out, lam=lam)
+        mu = torch.full((3, n - 1), float("nan"), dtype=torch.float64, device="cuda")
+        ctx.eeid_minor_eigvals(A, cols=[0, n // 2, n - 1], out=mu)
+        ctx.eeid_sync()
+        assert torch.isfinite(out).all() and torch.isfinite(lam).all() and torch.isfinite(mu).all()
+
+
+def test_batched_without_graphs_matches_graphs(torch_cuda, oracle_mod):
+    """eeid_set_graphs(0) plans and launches directly; results are bitwise those of
+    the captured-graph path."""
+    from paper_2002_04989_gb300 import eeid
+    torch = torch_cuda
+    mats = [inputs.batch_item(m, 8, 256)[1] for m in range(20, 28)]
+    outs = {}
+    for graphs in (True, False):
+        c = eeid.Context(0)
+        try:
+            c.eeid_set_graphs(graphs)
+            probs = [{"A": dev(torch, A), "out": torch.empty(A.shape, dtype=torch.float64, device="cuda")}
+                     for A in mats]
+            for _ in range(2):
+                c.eeid_components_batched(probs)
+            c.eeid_sync()
+            outs[graphs] = [p["out"].cpu().numpy() for p in probs]
+        finally:
+            c.close()
+    for a, b in zip(outs[True], outs[False]):
+        assert np.array_equal(a, b)
+
+
+def test_autotune_rejects_foreign_cache(torch_cuda, tmp_path):
+    """A cache written for another device model is ignored (re-tuned and rewritten)."""
+    from paper_2002_04989_gb300 import eeid
+    path = tmp_path / "tune.txt"
+    path.write_text("eeid-tune v1 sms=1 name=Some Other GPU\n1 4096 1 4\n")
+    c = eeid.Context(0)
+    try:
+        c.eeid_autotune(64, str(path))
+        head = path.read_text().splitlines()[0]
+        assert "Some Other GPU" not in head and head.startswith("eeid-tune v1")
+    finally:
+        c.close()
+
+
+def test_timing_misuse_and_tuning_errors(torch_cuda):
+    from paper_2002_04989_gb300 import eeid
+    c = eeid.Context(0)
+    try:
+        with pytest.raises(eeid.EeidError):
+            c.eeid_phase_times()                       # timing never enabled
+        with pytest.raises(eeid.EeidError):
+            c.eeid_tune_tridiag(1, 400, 0, 4)         # shared-memory variant above its limit
+        with pytest.raises(eeid.EeidError):
+            c.eeid_tune_tridiag(1, 100, 1, 3)         # unsupported warp count
+        with pytest.raises(eeid.EeidError):
+            c.eeid_autotune(0)
+    finally:
+        c.close()
