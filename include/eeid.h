@@ -142,6 +142,16 @@ eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* probs, in
  * directly (better when batch shapes never repeat, as in serving). */
 eeid_status eeid_set_graphs(eeid_ctx* ctx, int enable);
 
+/* Enable (default) or disable the tail overlap.  When one call's Householder
+ * reductions (A and its minors, Sec. 2) are near-equal in size and take more than
+ * one round of the persistent grid, the last, partial round is launched on an
+ * internal greatest-priority stream. Meanwhile the caller's stream bisects the
+ * eigenvalues of A and of the minors already reduced, on the SMs that round leaves
+ * idle.  The two streams join before the last minors' bisection, so the call still
+ * completes in the caller's stream order.  Results are bitwise the same either way;
+ * with the overlap on, the phase times of eeid_phase_times may overlap. */
+eeid_status eeid_set_overlap(eeid_ctx* ctx, int enable);
+
 /* Number of kernel launches the context has enqueued so far (for accounting). */
 int64_t eeid_launch_count(const eeid_ctx* ctx);
 
@@ -159,7 +169,7 @@ eeid_status eeid_tune_reset(eeid_ctx* ctx);
 
 /* Autotuner for the Householder kernel.  For size buckets up to min(max_m, 1024)
  * it times every supported variant (shared-memory or global-slot working matrix,
- * 1-8 warps per CTA) on a full wave of synthetic m x m minors on this device,
+ * 1-16 warps per CTA) on a full wave of synthetic m x m minors on this device,
  * keeps the fastest per bucket, and installs the choices as tuning rules (larger
  * sizes keep the built-in choice).  With `cache_path` non-NULL the table is read
  * from that file when it exists and was made on the same device model, and
@@ -183,7 +193,10 @@ eeid_status eeid_set_timing(eeid_ctx* ctx, int enable);
 
 /* Wait for the last timed call's events and write its per-phase device durations
  * in milliseconds into ms[0 .. min(cap, EEID_NUM_PHASES)) (0 for phases that call
- * did not run).  Returns the number of values written, or a negative status. */
+ * did not run).  A phase's duration runs from the start of its first launch to the
+ * end of its last; under the tail overlap (eeid_set_overlap) the reduction's
+ * interval contains part of the bisection phases.  Returns the number of values
+ * written, or a negative status. */
 int eeid_phase_times(eeid_ctx* ctx, double* ms, int cap);
 
 /* ------------------------------------------------------------------ serving

@@ -86,6 +86,11 @@ struct eeid_ctx {
   uint64_t graph_clock = 0;
   cudaStream_t cap_stream = nullptr;
   bool graphs_enabled = true;
+  // Tail overlap: the last round of a multi-round tridiagonalisation runs on aux_stream
+  // (greatest priority) while the caller's stream bisects the finished matrices.
+  bool overlap_enabled = true;
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   bool timing = false;
   cudaEvent_t ev[EEID_NUM_PHASES][2] = {};
   bool ran[EEID_NUM_PHASES] = {};
@@ -231,6 +236,18 @@ eeid_status ensure_stage(eeid_ctx* ctx, size_t bytes) {
   return EEID_OK;
 }
 
+// The context's greatest-priority stream and its fork/join events (tail overlap).
+eeid_status ensure_aux(eeid_ctx* ctx) {
+  if (ctx->aux_stream) return EEID_OK;
+  int least = 0, greatest = 0;
+  EEID_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priority range");
+  EEID_CK(cudaStreamCreateWithPriority(&ctx->aux_stream, cudaStreamNonBlocking, greatest),
+          "aux stream");
+  EEID_CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "fork event");
+  EEID_CK(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming), "join event");
+  return EEID_OK;
+}
+
 TriCfg tri_cfg(const eeid_ctx* ctx, int m) {
   for (auto it = ctx->rules.rbegin(); it != ctx->rules.rend(); ++it)
     if (m >= it->lo && m <= it->hi && cfg_supported(it->smem, it->warps, m))
@@ -250,10 +267,11 @@ int blocks_per_sm(eeid_ctx* ctx, const TriCfg& c, int max_m) {
 
 // Everything that determines a batched call's task lists and device pointers; two
 // calls with equal keys can replay the same CUDA graph.
-std::string batch_key(const std::vector<Problem>& probs, bool timing, int rules_version) {
+std::string batch_key(const std::vector<Problem>& probs, bool timing, int rules_version,
+                      bool overlap) {
   std::string k;
   auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
-  const int hdr[3] = {timing ? 1 : 0, rules_version, (int)probs.size()};
+  const int hdr[4] = {timing ? 1 : 0, rules_version, (int)probs.size(), overlap ? 1 : 0};
   put(hdr, sizeof hdr);
   for (const Problem& P : probs) {
     put(&P.dA, sizeof P.dA);
@@ -338,9 +356,34 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     g.counter_off = meta.take(sizeof(int));
     gplans.push_back(std::move(g));
   }
-  // bisection tasks: A's first (their eigenvalues seed the minors' brackets)
-  std::vector<int> bis_a, bis_m;
-  for (size_t t = 0; t < tri.size(); ++t) (tri[t].col < 0 ? bis_a : bis_m).push_back((int)t);
+  // Tail overlap.  One group of near-equal tasks (sizes within 1) in more than one
+  // round leaves grid - r CTAs idle through its last round (r = tasks mod grid).  Then
+  // the first tail_at tasks (whole rounds, every A among them) form the first launch;
+  // the last r run as a second launch on the context's greatest-priority stream, and
+  // meanwhile the caller's stream bisects A and the minors of the first launch on the
+  // SMs the tail leaves free.  Per-task arithmetic is unchanged.
+  int tail_at = 0, tail_grid = 0, tail_grid_of = 0;
+  size_t counter2_off = 0;
+  std::vector<char> in_tail(tri.size(), 0);
+  if (ctx->overlap_enabled && gplans.size() == 1 && mode != MODE_EIGVALS) {
+    const GroupPlan& g = gplans[0];
+    const int nt = (int)g.idx.size(), G = g.grid, r = nt % G;
+    const bool uniform = tri[g.idx.back()].m + 1 >= tri[g.idx.front()].m;
+    bool a_in_tail = false;   // every A must be done before the minors' brackets are set
+    for (int q = std::max(0, nt - r); q < nt; ++q) a_in_tail = a_in_tail || tri[g.idx[q]].col < 0;
+    if (nt > G && r > 0 && G - r >= std::max(1, G / 16) && uniform && !a_in_tail) {
+      tail_at = nt - r;
+      tail_grid = r;
+      tail_grid_of = G;
+      counter2_off = meta.take(sizeof(int));
+      for (int q = tail_at; q < nt; ++q) in_tail[g.idx[q]] = 1;
+    }
+  }
+  // bisection tasks: A's first (their eigenvalues seed the minors' brackets); with the
+  // tail overlap the minors of the tail are bisected in a second launch
+  std::vector<int> bis_a, bis_m, bis_m2;
+  for (size_t t = 0; t < tri.size(); ++t)
+    (tri[t].col < 0 ? bis_a : in_tail[t] ? bis_m2 : bis_m).push_back((int)t);
   const size_t bt_off = meta.take(sizeof(BisectTask) * tri.size());
   auto items_of = [&](const std::vector<int>& ts, std::vector<BisectItem>& items, int& mm) {
     std::vector<int> order = ts;
@@ -351,12 +394,17 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
       for (int k0 = 0; k0 < tri[t].m; k0 += kBisectThreads) items.push_back({t, k0});
     }
   };
-  std::vector<BisectItem> items_a, items_m;
-  int mm_a = 1, mm_m = 1;
+  std::vector<BisectItem> items_a, items_m, items_m2;
+  int mm_a = 1, mm_m = 1, mm_m2 = 1;
   items_of(bis_a, items_a, mm_a);
   items_of(bis_m, items_m, mm_m);
+  items_of(bis_m2, items_m2, mm_m2);
   const size_t bia_off = meta.take(sizeof(BisectItem) * std::max<size_t>(items_a.size(), 1));
-  const size_t bim_off = meta.take(sizeof(BisectItem) * std::max<size_t>(items_m.size(), 1));
+  // the minors' items, then the tail minors' items, in one array (one launch over both
+  // when the tail is not split off)
+  const size_t bim_off =
+      meta.take(sizeof(BisectItem) * std::max<size_t>(items_m.size() + items_m2.size(), 1));
+  const size_t bim2_off = bim_off + sizeof(BisectItem) * items_m.size();
   // identity
   std::vector<IdentityItem> iitems;
   size_t dt_off = 0, ip_off = 0, ii_off = 0;
@@ -400,9 +448,16 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     }
     for (auto& g : gplans)
       if (!g.cfg.smem) g.work_off = dat.take(sizeof(double) * g.slot * g.grid);
+    // fewer slots than planned: the tail would not be a round of them, so the group
+    // runs as one launch (both minor bisections then follow it)
+    if (tail_at > 0 && gplans[0].grid != tail_grid_of) tail_at = 0;
   }
   eeid_status st = ensure_ws(ctx, meta_bytes + dat.off);
   if (st != EEID_OK) return st;
+  if (tail_at > 0) {
+    st = ensure_aux(ctx);
+    if (st != EEID_OK) return st;
+  }
   char* ws = ctx->ws;
   char* wd = ws + meta_bytes;
   auto D = [&](size_t off) { return (double*)(wd + off); };
@@ -441,6 +496,13 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     }
     if (!items_a.empty()) memcpy(img + bia_off, items_a.data(), sizeof(BisectItem) * items_a.size());
     if (!items_m.empty()) memcpy(img + bim_off, items_m.data(), sizeof(BisectItem) * items_m.size());
+    if (!items_m2.empty())
+      memcpy(img + bim2_off, items_m2.data(), sizeof(BisectItem) * items_m2.size());
+    if (tail_at == 0) {   // tail dropped by the budget fit: one launch over both parts
+      items_m.insert(items_m.end(), items_m2.begin(), items_m2.end());
+      items_m2.clear();
+      mm_m = std::max(mm_m, mm_m2);
+    }
   }
   if (mode == MODE_COMPONENTS) {
     DenomTask* dt = (DenomTask*)(img + dt_off);
@@ -459,18 +521,18 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   auto enqueue_launches = [&]() -> eeid_status {
   // ---- launches (optionally bracketed by per-phase events)
   for (int ph = 0; ph < EEID_NUM_PHASES; ++ph) ctx->ran[ph] = false;
-  auto mark = [&](int ph, int which) -> cudaError_t {
+  auto mark = [&](int ph, int which, cudaStream_t on) -> cudaError_t {
     if (!ctx->timing) return cudaSuccess;
     if (which == 1) ctx->ran[ph] = true;
     // inside a capture the record must become a graph node (external event)
-    return ge ? cudaEventRecordWithFlags(ctx->ev[ph][which], stream, cudaEventRecordExternal)
-              : cudaEventRecord(ctx->ev[ph][which], stream);
+    return ge ? cudaEventRecordWithFlags(ctx->ev[ph][which], on, cudaEventRecordExternal)
+              : cudaEventRecord(ctx->ev[ph][which], on);
   };
-  EEID_CK(mark(EEID_PHASE_TRIDIAG, 0), "event");
+  EEID_CK(mark(EEID_PHASE_TRIDIAG, 0, stream), "event");
   for (auto& g : gplans) {
     TridiagLaunch L;
     L.tasks = (const TridiagTask*)(ws + g.task_off);
-    L.ntasks = (int)g.idx.size();
+    L.ntasks = tail_at > 0 ? tail_at : (int)g.idx.size();
     L.counter = (int*)(ws + g.counter_off);
     L.work = g.cfg.smem ? nullptr : D(g.work_off);
     L.work_stride = (int64_t)g.slot;
@@ -478,37 +540,63 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     L.status = ctx->d_status;
     EEID_CK(launch_tridiag(g.cfg.smem, g.cfg.warps, g.grid, L, stream), "tridiag launch");
     ctx->launches++;
+    if (tail_at > 0) {
+      // the tail: same slots (the first launch is done with them), its own counter
+      EEID_CK(cudaEventRecord(ctx->fork_ev, stream), "fork record");
+      EEID_CK(cudaStreamWaitEvent(ctx->aux_stream, ctx->fork_ev, 0), "fork wait");
+      L.tasks += tail_at;
+      L.ntasks = (int)g.idx.size() - tail_at;
+      L.counter = (int*)(ws + counter2_off);
+      EEID_CK(launch_tridiag(g.cfg.smem, g.cfg.warps, tail_grid, L, ctx->aux_stream),
+              "tridiag tail launch");
+      ctx->launches++;
+    }
   }
-  EEID_CK(mark(EEID_PHASE_TRIDIAG, 1), "event");
+  if (tail_at > 0) {
+    EEID_CK(mark(EEID_PHASE_TRIDIAG, 1, ctx->aux_stream), "event");
+    EEID_CK(cudaEventRecord(ctx->join_ev, ctx->aux_stream), "join record");
+  } else {
+    EEID_CK(mark(EEID_PHASE_TRIDIAG, 1, stream), "event");
+  }
   const BisectTask* btd = (const BisectTask*)(ws + bt_off);
   if (!items_a.empty()) {
-    EEID_CK(mark(EEID_PHASE_BISECT_A, 0), "event");
+    EEID_CK(mark(EEID_PHASE_BISECT_A, 0, stream), "event");
     EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bia_off), (int)items_a.size(), mm_a,
                           ctx->d_status, stream), "bisect(A) launch");
     ctx->launches++;
-    EEID_CK(mark(EEID_PHASE_BISECT_A, 1), "event");
+    EEID_CK(mark(EEID_PHASE_BISECT_A, 1, stream), "event");
   }
   if (mode == MODE_COMPONENTS) {
-    EEID_CK(mark(EEID_PHASE_DENOMINATORS, 0), "event");
+    EEID_CK(mark(EEID_PHASE_DENOMINATORS, 0, stream), "event");
     EEID_CK(launch_denominators((const DenomTask*)(ws + dt_off), (int)probs.size(), max_n,
                                 ctx->d_status, stream), "denominators launch");
     ctx->launches++;
-    EEID_CK(mark(EEID_PHASE_DENOMINATORS, 1), "event");
+    EEID_CK(mark(EEID_PHASE_DENOMINATORS, 1, stream), "event");
   }
-  if (!items_m.empty()) {
-    EEID_CK(mark(EEID_PHASE_BISECT_MINORS, 0), "event");
-    EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bim_off), (int)items_m.size(), mm_m,
-                          ctx->d_status, stream), "bisect(minors) launch");
-    ctx->launches++;
-    EEID_CK(mark(EEID_PHASE_BISECT_MINORS, 1), "event");
+  if (!items_m.empty() || !items_m2.empty()) {
+    EEID_CK(mark(EEID_PHASE_BISECT_MINORS, 0, stream), "event");
+    if (!items_m.empty()) {
+      EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bim_off), (int)items_m.size(), mm_m,
+                            ctx->d_status, stream), "bisect(minors) launch");
+      ctx->launches++;
+    }
+    if (tail_at > 0) EEID_CK(cudaStreamWaitEvent(stream, ctx->join_ev, 0), "join wait");
+    if (!items_m2.empty()) {
+      EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bim2_off), (int)items_m2.size(), mm_m2,
+                            ctx->d_status, stream), "bisect(tail minors) launch");
+      ctx->launches++;
+    }
+    EEID_CK(mark(EEID_PHASE_BISECT_MINORS, 1, stream), "event");
+  } else if (tail_at > 0) {
+    EEID_CK(cudaStreamWaitEvent(stream, ctx->join_ev, 0), "join wait");
   }
   if (mode == MODE_COMPONENTS && !iitems.empty()) {
-    EEID_CK(mark(EEID_PHASE_IDENTITY, 0), "event");
+    EEID_CK(mark(EEID_PHASE_IDENTITY, 0, stream), "event");
     EEID_CK(launch_identity((const IdentityProblem*)(ws + ip_off),
                             (const IdentityItem*)(ws + ii_off), (int)iitems.size(), max_n, stream),
             "identity launch");
     ctx->launches++;
-    EEID_CK(mark(EEID_PHASE_IDENTITY, 1), "event");
+    EEID_CK(mark(EEID_PHASE_IDENTITY, 1, stream), "event");
   }
     return EEID_OK;
   };
@@ -533,7 +621,8 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
       return lst;
     }
     if (e != cudaSuccess) return cuda_fail(e, "end capture");
-    e = cudaGraphInstantiate(&ge->exec, graph, 0);
+    // node priorities keep the tail launch ahead of the overlapping bisection
+    e = cudaGraphInstantiate(&ge->exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     ge->nkernels = (int)(ctx->launches - launches_before);
@@ -588,6 +677,9 @@ void eeid_ctx_destroy(eeid_ctx* ctx) {
   cudaDeviceSynchronize();
   clear_graphs(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -752,6 +844,13 @@ eeid_status eeid_set_graphs(eeid_ctx* ctx, int enable) {
   return EEID_OK;
 }
 
+eeid_status eeid_set_overlap(eeid_ctx* ctx, int enable) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  ctx->overlap_enabled = enable != 0;   // part of the graph key: no graph goes stale
+  return EEID_OK;
+}
+
 eeid_status eeid_tune_reset(eeid_ctx* ctx) {
   eeid_status st = check_ctx(ctx);
   if (st != EEID_OK) return st;
@@ -882,7 +981,7 @@ eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* in, int64
   EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   if (!ctx->graphs_enabled) return run(ctx, probs, MODE_COMPONENTS, s);
-  std::string key = batch_key(probs, ctx->timing, ctx->rules_version);
+  std::string key = batch_key(probs, ctx->timing, ctx->rules_version, ctx->overlap_enabled);
   for (auto& g : ctx->graphs) {
     if (g.key == key) {
       g.last_use = ++ctx->graph_clock;

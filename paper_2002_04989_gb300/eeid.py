@@ -82,6 +82,7 @@ SIGNATURES = {
     "eeid_phase_times": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
     "eeid_eigvals_noalloc": ([_vp, _i64, _i64, _vp, _vp], ctypes.c_int),
     "eeid_set_graphs": ([_vp, ctypes.c_int], ctypes.c_int),
+    "eeid_set_overlap": ([_vp, ctypes.c_int], ctypes.c_int),
     "eeid_server_create": ([ctypes.c_int, ctypes.POINTER(EeidServerOpts), ctypes.POINTER(_vp)],
                            ctypes.c_int),
     "eeid_server_destroy": ([_vp], None),
@@ -277,6 +278,9 @@ class Context:
 
     def eeid_set_graphs(self, enable: bool = True) -> int:
         return _check(self.lib.eeid_set_graphs(self.handle, 1 if enable else 0), False)
+
+    def eeid_set_overlap(self, enable: bool = True) -> int:
+        return _check(self.lib.eeid_set_overlap(self.handle, 1 if enable else 0), False)
 
     def launch_count(self) -> int:
         return int(self.lib.eeid_launch_count(self.handle))

@@ -406,3 +406,72 @@ def test_timing_misuse_and_tuning_errors(torch_cuda):
             c.eeid_autotune(0)
     finally:
         c.close()
+
+
+def _tail_expected(ntasks, grid):
+    """Whether a call with `ntasks` near-equal reductions on `grid` persistent CTAs splits
+    off its last partial round (the rule the planner applies)."""
+    r = ntasks % grid
+    return ntasks > grid and r > 0 and grid - r >= max(1, grid // 16)
+
+
+def test_tail_overlap_bitwise_and_launches(torch_cuda, oracle_mod):
+    """n = 520: 521 near-equal reductions at one CTA per SM take several rounds.  With
+    the tail overlap the last round is a second launch on another stream, bisection
+    overlaps it, and the tail minors are bisected in a second launch: two more kernel
+    launches, bitwise the same grid and eigenvalues as with the overlap off, in direct
+    calls and in captured batched calls."""
+    from paper_2002_04989_gb300 import eeid
+    torch = torch_cuda
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    p = inputs.planted(520, 21, -1.0, 1.0, 1e-3)
+    dA = dev(torch, p.A)
+    res = {}
+    for overlap in (False, True):
+        c = eeid.Context(0)
+        try:
+            c.eeid_set_overlap(overlap)
+            lam = torch.empty(520, dtype=torch.float64, device="cuda")
+            l0 = c.launch_count()
+            out = c.eeid_components(dA, lam=lam)
+            c.eeid_sync()
+            nl = c.launch_count() - l0
+            probs = [{"A": dA, "out": torch.empty((520, 520), dtype=torch.float64, device="cuda"),
+                      "lam": torch.empty(520, dtype=torch.float64, device="cuda")}]
+            c.eeid_set_timing(True)
+            for _ in range(2):                      # capture, then replay
+                c.eeid_components_batched(probs)
+                ph = c.eeid_phase_times()
+                assert all(ph[k] > 0 for k in ("tridiag", "bisect_A", "bisect_minors", "identity"))
+            c.eeid_set_timing(False)
+            c.eeid_sync()
+            assert np.array_equal(probs[0]["out"].cpu().numpy(), out.cpu().numpy())
+            assert np.array_equal(probs[0]["lam"].cpu().numpy(), lam.cpu().numpy())
+            res[overlap] = (out.cpu().numpy(), lam.cpu().numpy(), nl)
+        finally:
+            c.close()
+    assert np.array_equal(res[True][0], res[False][0]) and np.array_equal(res[True][1], res[False][1])
+    assert res[False][2] == 5
+    assert res[True][2] == (7 if _tail_expected(521, sms) else 5)
+    assert np.max(np.abs(res[True][0] - (p.Q * p.Q).T)) <= TOL_VSQ
+
+
+def test_tail_overlap_off_when_budget_shrinks_grid(torch_cuda):
+    """A budget that leaves fewer working slots than SMs changes the round structure;
+    the call then runs its reductions as one launch and still matches bitwise."""
+    from paper_2002_04989_gb300 import eeid
+    torch = torch_cuda
+    A = inputs.goe(520, 22)
+    dA = dev(torch, A)
+    outs, launches = [], []
+    for budget in (0, 200 << 20):
+        c = eeid.Context(0, budget)
+        try:
+            l0 = c.launch_count()
+            outs.append(c.eeid_components(dA).cpu().numpy())
+            c.eeid_sync()
+            launches.append(c.launch_count() - l0)
+        finally:
+            c.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert launches[1] == 5
