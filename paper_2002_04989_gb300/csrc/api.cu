@@ -255,6 +255,18 @@ TriCfg tri_cfg(const eeid_ctx* ctx, int m) {
   return tri_cfg_default(m);
 }
 
+bool rule_covers(const eeid_ctx* ctx, int m) {
+  for (const auto& r : ctx->rules)
+    if (m >= r.lo && m <= r.hi) return true;
+  return false;
+}
+
+// Time of one round of the 8-warp global variant at two CTAs per SM (twice the
+// matrices) over one round of the 16-warp variant at one CTA per SM, measured on
+// GB300 at m = 1023 (the second warp group's reduction and reflector phases overlap
+// the first's tile pass, so the FP64 pipe stays busier).
+constexpr double kRound8x2Per16 = 1.89;
+
 int blocks_per_sm(eeid_ctx* ctx, const TriCfg& c, int max_m) {
   int& cache = ctx->occ_cache[c.smem ? 0 : 1][c.warps];
   int& cm = ctx->occ_m[c.smem ? 0 : 1][c.warps];
@@ -362,21 +374,57 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   // the last r run as a second launch on the context's greatest-priority stream, and
   // meanwhile the caller's stream bisects A and the minors of the first launch on the
   // SMs the tail leaves free.  Per-task arithmetic is unchanged.
+  //
+  // Hybrid rounds.  When such a group runs one 16-warp CTA per SM by default and the
+  // 8-warp variant fits two CTAs per SM, whole rounds of the 8-warp pair are faster
+  // (kRound8x2Per16 < 2); the group then runs its whole pair-rounds that way and a
+  // tail of at most one round as the 16-warp second launch.  Both variants give
+  // bitwise the same (d, e), so the plan never shows in the results.
   int tail_at = 0, tail_grid = 0, tail_grid_of = 0;
+  TriCfg tail_cfg{false, 0};
   size_t counter2_off = 0;
   std::vector<char> in_tail(tri.size(), 0);
   if (ctx->overlap_enabled && gplans.size() == 1 && mode != MODE_EIGVALS) {
-    const GroupPlan& g = gplans[0];
-    const int nt = (int)g.idx.size(), G = g.grid, r = nt % G;
+    GroupPlan& g = gplans[0];
+    const int nt = (int)g.idx.size();
     const bool uniform = tri[g.idx.back()].m + 1 >= tri[g.idx.front()].m;
-    bool a_in_tail = false;   // every A must be done before the minors' brackets are set
-    for (int q = std::max(0, nt - r); q < nt; ++q) a_in_tail = a_in_tail || tri[g.idx[q]].col < 0;
-    if (nt > G && r > 0 && G - r >= std::max(1, G / 16) && uniform && !a_in_tail) {
-      tail_at = nt - r;
-      tail_grid = r;
-      tail_grid_of = G;
+    // every A must be done before the minors' brackets are set
+    auto a_from = [&](int q0) {
+      for (int q = std::max(0, q0); q < nt; ++q)
+        if (tri[g.idx[q]].col < 0) return true;
+      return false;
+    };
+    auto split_at = [&](int at, int grid) {
+      tail_at = at;
+      tail_grid = grid;
+      tail_grid_of = g.grid;
       counter2_off = meta.take(sizeof(int));
-      for (int q = tail_at; q < nt; ++q) in_tail[g.idx[q]] = 1;
+      for (int q = at; q < nt; ++q) in_tail[g.idx[q]] = 1;
+    };
+    bool hybrid = false;
+    const TriCfg c8{false, 8};
+    if (uniform && !g.cfg.smem && g.cfg.warps >= 12 && !rule_covers(ctx, g.max_m) &&
+        cfg_supported(false, 8, g.max_m)) {
+      const int b8 = blocks_per_sm(ctx, c8, g.max_m);
+      const int G8 = ctx->sms * b8, G16 = g.grid;
+      const int bulk = nt / G8 * G8, r = nt - bulk;
+      const double t_hybrid = (double)(bulk / G8) * kRound8x2Per16 + (r > 0 ? 1.0 : 0.0);
+      const double t_plain = (double)((nt + G16 - 1) / G16);
+      if (b8 >= 2 && G16 == ctx->sms && bulk > 0 && r <= G16 && t_hybrid < t_plain &&
+          !a_from(bulk)) {
+        hybrid = true;
+        tail_cfg = g.cfg;
+        g.cfg = c8;
+        g.grid = G8;
+        if (r > 0) split_at(bulk, r);
+      }
+    }
+    if (!hybrid) {
+      const int G = g.grid, r = nt % G;
+      if (nt > G && r > 0 && G - r >= std::max(1, G / 16) && uniform && !a_from(nt - r)) {
+        tail_cfg = g.cfg;
+        split_at(nt - r, r);
+      }
     }
   }
   // bisection tasks: A's first (their eigenvalues seed the minors' brackets); with the
@@ -547,7 +595,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
       L.tasks += tail_at;
       L.ntasks = (int)g.idx.size() - tail_at;
       L.counter = (int*)(ws + counter2_off);
-      EEID_CK(launch_tridiag(g.cfg.smem, g.cfg.warps, tail_grid, L, ctx->aux_stream),
+      EEID_CK(launch_tridiag(tail_cfg.smem, tail_cfg.warps, tail_grid, L, ctx->aux_stream),
               "tridiag tail launch");
       ctx->launches++;
     }

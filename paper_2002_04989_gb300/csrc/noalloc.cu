@@ -29,7 +29,7 @@ namespace {
 constexpr int kNoAllocMaxN = 512;
 constexpr int kNoAllocWarps = 4;
 constexpr size_t kNb = (kNoAllocMaxN + 31) / 32;
-constexpr size_t kSlotDoubles = (size_t)kNoAllocMaxN * kNoAllocMaxN + kNb * kNb * 32 + kNb * 16 * 32 + 32;
+constexpr size_t kSlotDoubles = (size_t)kNoAllocMaxN * kNoAllocMaxN + 2 * kNb * kNb * 32 + 32;
 constexpr size_t kDEDoubles = 2 * (size_t)kNoAllocMaxN;         // d[n], e[n-1]
 constexpr size_t kMetaDoubles = 64;                              // 512 bytes of descriptors
 constexpr size_t kScratchDoubles = kSlotDoubles + kDEDoubles + kMetaDoubles;

@@ -19,7 +19,10 @@
 // from a conflict-free shared-memory copy and along columns in registers.
 //
 // Determinism: every partial sum has one owner and a fixed summation order, so a
-// matrix's (d, e) do not depend on which CTA, batch or launch processed it.
+// matrix's (d, e) do not depend on which CTA, batch or launch processed it.  In the
+// global-slot variant every tile keeps its own row and column partials, which are
+// summed in tile order, so the result does not depend on the warp count either: the
+// 2-16-warp instantiations give bitwise the same (d, e).
 //
 // Two storage variants share the code:
 //   SMEM = true   the whole working matrix lives in shared memory (m <= 160);
@@ -43,24 +46,22 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum over the CTA; every thread receives the total.  Every FP64 warp instruction
-// costs the same FP64 issue time however many lanes are active, so the partials go
-// to shared memory and one warp adds them (W + 5 FP64 instructions in total).
-// `red` holds W*32 + 1 doubles.
-template <int W>
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  red[threadIdx.x] = v;
-  __syncthreads();
-  if (warp == 0) {
-    double s = red[lane];
-#pragma unroll
-    for (int w = 1; w < W; ++w) s += red[w * 32 + lane];
-    s = warp_sum(s);
-    if (lane == 0) red[W * 32] = s;
+// sum_{i in [i0, m)} x_i y_i by one warp, in an order fixed by (i0, m) alone: lane l
+// takes i = i0 + l, i0 + l + 32, ... in four interleaved chains, then a shuffle tree.
+// Only warp 0 calls it, so the reductions of a step do not depend on the CTA's warp
+// count (and cost the FP64 issue of (m - i0)/32 + 8 warp instructions).
+__device__ __forceinline__ double warp_dot(const double* x, const double* y, int i0, int m,
+                                           int lane) {
+  double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+  int i = i0 + lane;
+  for (; i + 96 < m; i += 128) {
+    q0 = fma(x[i], y[i], q0);
+    q1 = fma(x[i + 32], y[i + 32], q1);
+    q2 = fma(x[i + 64], y[i + 64], q2);
+    q3 = fma(x[i + 96], y[i + 96], q3);
   }
-  __syncthreads();
-  return red[W * 32];
+  for (; i < m; i += 32) q0 = fma(x[i], y[i], q0);
+  return warp_sum((q0 + q1) + (q2 + q3));
 }
 
 // One 32x32 tile of the fused pass: rows [R0, R0+32), columns [C0, C0+32) of the
@@ -136,7 +137,11 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
   }
   *tslot = t0 + t1;
   __syncwarp();
-  // row half: u_i += sum_{c <= i} a_ic v_c (four chains carried across the block-row)
+  // row half: u_i += sum_{c <= i} a_ic v_c.  Shared-memory variant: four chains carried
+  // across the block-row.  Global variant: one chain per tile (u[0], stored per tile);
+  // with 16 warps on the SM a warp gets an FP64 issue slot only every few hundred
+  // cycles, so the chain's latency is hidden and no per-tile combine is needed.
+  constexpr int NCH = SMEM ? 4 : 1;
   const int i = R0 + lane;
   const int ir = EDGE ? min(i, m - 1) : i;   // clamped row address for the shared copy
   const double* rowp = SMEM ? (S + (size_t)ir * ld + C0) : (tile + lane * TP);
@@ -144,7 +149,7 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
   for (int cc = 0; cc < T; ++cc) {
     const bool ok = !EDGE || (i < m && C0 + cc <= i);
     const double x = ok ? rowp[cc] : 0.0;
-    u[cc & 3] = fma(x, vC[C0 + cc], u[cc & 3]);
+    u[cc & (NCH - 1)] = fma(x, vC[C0 + cc], u[cc & (NCH - 1)]);
   }
   __syncwarp();
 }
@@ -200,7 +205,7 @@ __device__ __forceinline__ void diag_tile(double* S, int64_t ld, int m, int R0, 
   for (int cc = 0; cc < 32; ++cc) {
     const bool ok = i < nrows && cc < nrows;
     const double x = ok ? tile[i * TP + cc] : 0.0;
-    u[cc & 3] = fma(x, vC[R0 + cc], u[cc & 3]);
+    u[0] = fma(x, vC[R0 + cc], u[0]);   // one chain (global variant, see tile_step)
   }
   __syncwarp();
 }
@@ -251,8 +256,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
   double* wP = vP + Ly.VM;
   double* vC = wP + Ly.VM;
   double* const wC = wP;
-  double* red = vC + Ly.VM;       // W*32 + 1 reduction slots (+ padding)
-  double* scal = red + W * 32 + 8;  // 8 scalars
+  double* scal = vC + Ly.VM;      // 8 scalars
   double* S;
   double* tpart;
   double* upart;
@@ -310,7 +314,6 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
       const int base = k + 1;
       const bool upd = (k > 0);
       // ---- Phase A: apply update k-1 to column k; x = column below the diagonal.
-      double sig = 0;
       const double vPk = upd ? vP[k] : 0.0, wPk = upd ? wP[k] : 0.0;
       for (int i = k + tid; i < m; i += NT) {
         double a = S[(size_t)i * ld + k];
@@ -322,12 +325,13 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
           vC[i] = 1.0;
         } else {
           vC[i] = a;
-          sig = fma(a, a, sig);
         }
       }
-      sig = block_sum<W>(sig, red);
-      // ---- Phase B: reflector scalars (warp 0), broadcast through shared memory.
+      __syncthreads();
+      // ---- Phase B: sigma = |x|^2 and the reflector scalars (warp 0), broadcast
+      // through shared memory.
       if (warp == 0) {
+        const double sig = warp_dot(vC, vC, k + 2, m, lane);
         const double alpha = scal[0];
         double tau = 0.0, scale = 0.0, beta = alpha;
         if (sig != 0.0) {
@@ -373,17 +377,17 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
           upart[I * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
         }
       } else {
-        // contiguous, balanced range of tiles; a block-row split between warps leaves
-        // one row partial per warp (upart[(I*16 + w)*32 + l]), summed in warp order
+        // contiguous, balanced range of tiles per warp; each tile leaves its column
+        // partial in tpart and its row partial in upart (both indexed by tile)
         const int T = nb * (nb + 1) / 2;
         const int t0 = tile_start(warp, T, W), t1 = tile_start(warp + 1, T, W);
         int I = 0;
         while ((I + 1) * (I + 2) / 2 <= t0) ++I;
         int J = t0 - I * (I + 1) / 2;
-        double u[4] = {0.0, 0.0, 0.0, 0.0};
         for (int t = t0; t < t1; ++t) {
           const int R0 = base + kTile * I, C0 = base + kTile * J;
           double* tslot = tpart + ((size_t)I * nbmax + J) * 32 + lane;
+          double u[4] = {0.0, 0.0, 0.0, 0.0};
           if (J < I && R0 + kTile <= m) {
             if (upd) tile_step<SMEM, false, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
             else     tile_step<SMEM, false, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
@@ -394,39 +398,35 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
             if (upd) tile_step<SMEM, true, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
             else     tile_step<SMEM, true, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, u);
           }
-          if (J == I || t == t1 - 1) {
-            upart[((size_t)I * 16 + warp) * 32 + lane] = (u[0] + u[1]) + (u[2] + u[3]);
-            u[0] = u[1] = u[2] = u[3] = 0.0;
-          }
+          upart[((size_t)I * nbmax + J) * 32 + lane] = u[0];
           if (++J > I) { ++I; J = 0; }
         }
       }
       __syncthreads();
       // ---- Phase E: p = tau * (row partials + column partials); gamma = tau/2 p.v
-      double dot = 0.0;
       for (int i = base + tid; i < m; i += NT) {
         const int r = i - base, I = r >> 5, l = r & 31;
         double p;
         if (SMEM) {
           p = upart[I * 32 + l];
         } else {
-          // warps whose tile ranges meet block-row I, in warp order
-          const int T = nb * (nb + 1) / 2, ta = I * (I + 1) / 2, tb = ta + I;
-          p = 0.0;
-          for (int w = 0; w < W; ++w) {
-            const int s0 = tile_start(w, T, W), s1 = tile_start(w + 1, T, W);
-            if (s0 < s1 && s0 <= tb && s1 > ta) p += upart[((size_t)I * 16 + w) * 32 + l];
-          }
+          // row partials of the tiles of block-row I, in tile order
+          const double* up = upart + (size_t)I * nbmax * 32 + l;
+          p = up[0];
+          for (int J = 1; J <= I; ++J) p += up[(size_t)J * 32];
         }
         for (int I2 = I; I2 < nb; ++I2) p += tpart[((size_t)I2 * nbmax + I) * 32 + l];
-        p *= tau;
-        wC[i] = p;
-        dot = fma(p, vC[i], dot);
+        wC[i] = p * tau;
       }
-      dot = block_sum<W>(dot, red);
+      __syncthreads();
+      if (warp == 0) {
+        const double dot = warp_dot(wC, vC, base, m, lane);
+        if (lane == 0) scal[3] = 0.5 * tau * dot;
+      }
+      __syncthreads();
       // ---- Phase F: w = p - gamma v.
       {
-        const double gamma = 0.5 * tau * dot;
+        const double gamma = scal[3];
         for (int i = base + tid; i < m; i += NT) wC[i] = fma(-gamma, vC[i], wC[i]);
       }
       __syncthreads();
@@ -460,12 +460,12 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
 
 size_t tridiag_global_slot_doubles(int max_m) {
   const Layout L = make_layout(false, max_m);
-  return (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 16 * 32 + 32;
+  return (size_t)max_m * L.ld + 2 * (size_t)L.nbmax * L.nbmax * 32 + 32;
 }
 
 size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps) {
   const Layout L = make_layout(smem_path, max_m);
-  size_t d = 3 * (size_t)L.VM + (size_t)warps * 32 + 8 + 8;
+  size_t d = 3 * (size_t)L.VM + 8;
   if (smem_path)
     d += (size_t)max_m * L.ld + (size_t)L.nbmax * L.nbmax * 32 + (size_t)L.nbmax * 32;
   else

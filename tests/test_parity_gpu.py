@@ -475,3 +475,29 @@ def test_tail_overlap_off_when_budget_shrinks_grid(torch_cuda):
             c.close()
     assert np.array_equal(outs[0], outs[1])
     assert launches[1] == 5
+
+
+@pytest.mark.parametrize("n,path,warps", [(300, 1, (2, 4, 8, 12, 16)), (700, 1, (4, 8, 12, 16)),
+                                          (100, 0, (1, 2, 4, 8))])
+def test_warp_count_does_not_change_results(torch_cuda, n, path, warps):
+    """Every instantiation of one storage variant gives bitwise the same grid: partial
+    sums are kept per tile and reduced in an order fixed by the matrix size alone, so
+    the scheduler may run a matrix with any warp count."""
+    from paper_2002_04989_gb300 import eeid
+    torch = torch_cuda
+    dA = dev(torch, inputs.goe(n, 40 + n))
+    lo = 161 if path == 1 else 1
+    hi = 2048 if path == 1 else 160
+    ref = None
+    for W in warps:
+        c = eeid.Context(0)
+        try:
+            c.eeid_tune_tridiag(lo, hi, path, W)
+            out = c.eeid_components(dA).cpu().numpy()
+            c.eeid_sync()
+        finally:
+            c.close()
+        if ref is None:
+            ref = out
+        else:
+            assert np.array_equal(out, ref), W
