@@ -107,14 +107,16 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
         if (ok) dst[(size_t)rr * ld] = a[rr];
       }
     }
-    // t_c = sum_{i > c} a_ic v_i (two independent chains)
+    // t_c = sum_{i > c} a_ic v_i (shared-memory variant: two chains; global variant:
+    // one, for the reason given at the row half below)
 #pragma unroll
     for (int rr = 0; rr < 16; rr += 2) {
       const int i = R0 + h + rr;
       const double x0 = (!EDGE || i > c) ? a[rr] : 0.0;
       const double x1 = (!EDGE || i + 1 > c) ? a[rr + 1] : 0.0;
       t0 = fma(x0, vC[i], t0);
-      t1 = fma(x1, vC[i + 1], t1);
+      if (SMEM) t1 = fma(x1, vC[i + 1], t1);
+      else      t0 = fma(x1, vC[i + 1], t0);
     }
     if (!SMEM) {
 #pragma unroll
@@ -135,7 +137,7 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
       if (!SMEM) tile[rr * TP + lane] = a;
     }
   }
-  *tslot = t0 + t1;
+  *tslot = SMEM ? t0 + t1 : t0;
   __syncwarp();
   // row half: u_i += sum_{c <= i} a_ic v_c.  Shared-memory variant: four chains carried
   // across the block-row.  Global variant: one chain per tile (u[0], stored per tile);
