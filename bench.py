@@ -44,10 +44,11 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 # flops per m x m matrix) for one step: A (m = n) plus n minors (m = n - 1).
 TRIDIAG_FLOPS = 4.0 / 3.0 * (N ** 3 + N * (N - 1) ** 3)
 
-# DRAM traffic of one k_tridiag launch from an ncu capture (profiles/), valid only
-# while the kernel source is unchanged (sha256 of csrc/tridiag.cu at capture time).
-TRIDIAG_TRAFFIC = {"bytes_per_launch": 2.990e12,
-                   "source_sha256": "e518c37a446d48c2f77408600cbeb334928e98f28d49b08d116029fba5923d79"}
+# DRAM traffic of the tridiagonalisation phase of one step (all its launches), from an
+# ncu capture scaled by the work (profiles/), valid only while the kernel source is
+# unchanged (sha256 of csrc/tridiag.cu at capture time).
+TRIDIAG_TRAFFIC = {"bytes_per_launch": 3.195e12,
+                   "source_sha256": "c25ea769261f1f23fc3462abc76eafd40e72b94c096127e3e0ecbace02a90be0"}
 
 
 def src_sha(path: str) -> str:
@@ -299,7 +300,9 @@ def run_gpu(args, world, rank, local):
         "config": {"workload": WORKLOAD, "n": N, "components_per_step_per_gpu": N * N,
                    "l2": "flushed between steps (256 MiB write, inside the timed region)",
                    "parallelism": f"replicas x{world} (weak scaling, no collective)"},
-        "roofline": {"bound": "alu", "kernel": "k_tridiag (FP64 Householder, A + 1024 minors)",
+        "roofline": {"bound": "alu",
+                     "kernel": "k_tridiag (FP64 Householder, A + 1024 minors: 8-warp pair "
+                               "rounds + 16-warp tail; time = the phase's span)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz "
