@@ -501,3 +501,26 @@ def test_warp_count_does_not_change_results(torch_cuda, n, path, warps):
             ref = out
         else:
             assert np.array_equal(out, ref), W
+
+
+def test_hybrid_rounds_bitwise_at_benchmark_size(torch_cuda):
+    """n = 1024, all 1024 columns: 1025 near-equal reductions are planned as rounds of two
+    8-warp CTAs per SM plus a 16-warp tail overlapped with the bisection.  The grid and
+    eigenvalues are bitwise those of the plain plan (overlap off: one 16-warp launch)."""
+    from paper_2002_04989_gb300 import eeid
+    torch = torch_cuda
+    p = inputs.planted1024()
+    dA = dev(torch, p.A)
+    res = []
+    for overlap in (True, False):
+        c = eeid.Context(0)
+        try:
+            c.eeid_set_overlap(overlap)
+            lam = torch.empty(1024, dtype=torch.float64, device="cuda")
+            out = c.eeid_components(dA, lam=lam)
+            c.eeid_sync()
+            res.append((out.cpu().numpy(), lam.cpu().numpy()))
+        finally:
+            c.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert np.max(np.abs(res[0][0] - (p.Q * p.Q).T)) <= TOL_VSQ
