@@ -202,11 +202,13 @@ int eeid_phase_times(eeid_ctx* ctx, double* ms, int cap);
 /* ------------------------------------------------------------------ serving
  * A request loop with continuous batching.  Callers on any thread submit a host
  * matrix and the components they want; a scheduler thread admits requests in
- * arrival order while the device budget allows, merges all admitted waiting
- * requests into one batched launch (the work of eeid_components_batched), and keeps
- * up to `max_inflight` batches on the GPU at once, each on its own stream and
- * workspace, so requests arriving while a batch runs start as soon as a slot and
- * memory free up and overlap it.  A request's matrix, output and eigenvalues stay
+ * arrival order while the device budget allows, merges waiting requests of similar
+ * cost (within a factor of 8 of n^3 (columns + 1)) into one batched launch (the work
+ * of eeid_components_batched), and keeps up to `max_inflight` batches on the GPU at
+ * once, each on its own stream and workspace, so requests arriving while a batch
+ * runs start as soon as a slot and memory free up.  Each batch's reductions are
+ * launched one round of the grid at a time, so a large request holds up a small one
+ * by about one round, not its whole run.  A request's matrix, output and eigenvalues stay
  * resident on the device until its results are copied back.  Each result is
  * bitwise the same as eeid_components on that matrix alone.  (The paper serves one
  * component per call; this is the build's own serving form of Eq. 1.) */

@@ -89,6 +89,11 @@ struct eeid_ctx {
   // Tail overlap: the last round of a multi-round tridiagonalisation runs on aux_stream
   // (greatest priority) while the caller's stream bisects the finished matrices.
   bool overlap_enabled = true;
+  // Round launches (serving): each group's persistent reduction is cut into launches
+  // of at most one round of tasks, so kernels of other streams get SMs between them.
+  bool round_launches = false;
+  // SMs the persistent reductions leave free (serving: room for a second batch).
+  int sm_reserve = 0;
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   bool timing = false;
@@ -280,10 +285,10 @@ int blocks_per_sm(eeid_ctx* ctx, const TriCfg& c, int max_m) {
 // Everything that determines a batched call's task lists and device pointers; two
 // calls with equal keys can replay the same CUDA graph.
 std::string batch_key(const std::vector<Problem>& probs, bool timing, int rules_version,
-                      bool overlap) {
+                      int plan_flags) {
   std::string k;
   auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
-  const int hdr[4] = {timing ? 1 : 0, rules_version, (int)probs.size(), overlap ? 1 : 0};
+  const int hdr[4] = {timing ? 1 : 0, rules_version, (int)probs.size(), plan_flags};
   put(hdr, sizeof hdr);
   for (const Problem& P : probs) {
     put(&P.dA, sizeof P.dA);
@@ -349,8 +354,8 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   // tridiagonalisation groups (one persistent launch per configuration)
   std::vector<std::vector<int>> groups(64);
   for (size_t t = 0; t < tri.size(); ++t) groups[cfg_key(tri_cfg(ctx, tri[t].m))].push_back((int)t);
-  struct GroupPlan { TriCfg cfg; int max_m; int grid; size_t task_off, counter_off, work_off;
-                     size_t slot; std::vector<int> idx; };
+  struct GroupPlan { TriCfg cfg; int max_m; int grid; int nchunks; size_t task_off, counter_off,
+                     work_off; size_t slot; std::vector<int> idx; };
   std::vector<GroupPlan> gplans;
   for (int key = 0; key < 64; ++key) {
     if (groups[key].empty()) continue;
@@ -361,11 +366,13 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     g.max_m = tri[g.idx[0]].m;
     g.cfg = tri_cfg(ctx, g.max_m);
     const int bps = blocks_per_sm(ctx, g.cfg, g.max_m);
-    g.grid = (int)std::min<int64_t>((int64_t)g.idx.size(), (int64_t)ctx->sms * bps);
+    const int sms_used = std::max(1, ctx->sms - ctx->sm_reserve);
+    g.grid = (int)std::min<int64_t>((int64_t)g.idx.size(), (int64_t)sms_used * bps);
     g.slot = g.cfg.smem ? 0 : tridiag_global_slot_doubles(g.max_m);
     g.work_off = 0;  // assigned after the rest of the layout (see below)
     g.task_off = meta.take(sizeof(TridiagTask) * g.idx.size());
-    g.counter_off = meta.take(sizeof(int));
+    g.nchunks = ctx->round_launches ? (int)((g.idx.size() + g.grid - 1) / g.grid) : 1;
+    g.counter_off = meta.take(sizeof(int) * g.nchunks);
     gplans.push_back(std::move(g));
   }
   // Tail overlap.  One group of near-equal tasks (sizes within 1) in more than one
@@ -384,7 +391,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   TriCfg tail_cfg{false, 0};
   size_t counter2_off = 0;
   std::vector<char> in_tail(tri.size(), 0);
-  if (ctx->overlap_enabled && gplans.size() == 1 && mode != MODE_EIGVALS) {
+  if (ctx->overlap_enabled && !ctx->round_launches && gplans.size() == 1 && mode != MODE_EIGVALS) {
     GroupPlan& g = gplans[0];
     const int nt = (int)g.idx.size();
     const bool uniform = tri[g.idx.back()].m + 1 >= tri[g.idx.front()].m;
@@ -586,6 +593,22 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     L.work_stride = (int64_t)g.slot;
     L.max_m = g.max_m;
     L.status = ctx->d_status;
+    if (g.nchunks > 1) {
+      // round launches: chunk c takes tasks [c*chunk, ...) with its own counter
+      const int total = L.ntasks, chunk = (total + g.nchunks - 1) / g.nchunks;
+      const TridiagTask* t0 = L.tasks;
+      for (int c = 0; c < g.nchunks; ++c) {
+        const int a = c * chunk, b = std::min(total, a + chunk);
+        if (a >= b) break;
+        L.tasks = t0 + a;
+        L.ntasks = b - a;
+        L.counter = (int*)(ws + g.counter_off) + c;
+        EEID_CK(launch_tridiag(g.cfg.smem, g.cfg.warps, std::min(g.grid, b - a), L, stream),
+                "tridiag launch");
+        ctx->launches++;
+      }
+      continue;
+    }
     EEID_CK(launch_tridiag(g.cfg.smem, g.cfg.warps, g.grid, L, stream), "tridiag launch");
     ctx->launches++;
     if (tail_at > 0) {
@@ -711,6 +734,10 @@ eeid_status eeid_ctx_create(int device, size_t hbm_budget_bytes, eeid_ctx** out)
   e = cudaMalloc((void**)&c->d_status, 256);
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 256);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+  // every kernel loaded now, not at its first launch (see preload_tridiag)
+  if (e == cudaSuccess) e = preload_tridiag();
+  if (e == cudaSuccess) e = preload_bisect();
+  if (e == cudaSuccess) e = preload_identity();
   if (e != cudaSuccess) {
     eeid_ctx_destroy(c);
     return cuda_fail(e, "context setup");
@@ -892,6 +919,35 @@ eeid_status eeid_set_graphs(eeid_ctx* ctx, int enable) {
   return EEID_OK;
 }
 
+}  // extern "C"
+
+namespace eeid {
+eeid_status set_round_launches(eeid_ctx* ctx, int enable) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  ctx->round_launches = enable != 0;
+  return EEID_OK;
+}
+
+eeid_status reserve_workspace(eeid_ctx* ctx, size_t device_bytes, size_t staging_bytes) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  st = ensure_ws(ctx, std::min(device_bytes, ctx->budget));
+  if (st == EEID_OK) st = ensure_stage(ctx, staging_bytes);
+  return st;
+}
+
+eeid_status set_sm_reserve(eeid_ctx* ctx, int sms) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  ctx->sm_reserve = std::max(0, std::min(sms, ctx->sms - 1));
+  return EEID_OK;
+}
+}  // namespace eeid
+
+extern "C" {
+
 eeid_status eeid_set_overlap(eeid_ctx* ctx, int enable) {
   eeid_status st = check_ctx(ctx);
   if (st != EEID_OK) return st;
@@ -1029,7 +1085,8 @@ eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* in, int64
   EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   if (!ctx->graphs_enabled) return run(ctx, probs, MODE_COMPONENTS, s);
-  std::string key = batch_key(probs, ctx->timing, ctx->rules_version, ctx->overlap_enabled);
+  std::string key = batch_key(probs, ctx->timing, ctx->rules_version,
+                              (ctx->overlap_enabled ? 1 : 0) | (ctx->round_launches ? 2 : 0));
   for (auto& g : ctx->graphs) {
     if (g.key == key) {
       g.last_use = ++ctx->graph_clock;

@@ -28,10 +28,10 @@
 //    read as a warp-wide broadcast; each warp loops until a warp vote finds every
 //    lane converged.
 //  * Two phases.  FP32 runs at ~60x the FP64 rate on this part, so the bracket is
-//    first narrowed to ~2^-41 ||T|| with Sturm counts in double-float arithmetic
+//    first narrowed to ~2^-36 ||T|| with Sturm counts in double-float arithmetic
 //    (pairs of FP32 values, ~2^-44 relative per operation).  The FP64 phase then
-//    widens that bracket by 2^-40 ||T||, re-verifies it with two exact-FP64 Sturm
-//    counts and finishes the bisection in FP64.  A bracket that fails the check
+//    widens that bracket by 2^-40 ||T|| (more than the double-float counts' error),
+//    re-verifies it with two exact-FP64 Sturm counts and finishes in FP64.  A bracket that fails the check
 //    (the cheap phase misjudged, or the interlacing seed was wrong) falls back to
 //    the Gershgorin bracket, so the result never depends on the FP32 phase.
 //  * The two verifying counts also return det(T - xI) at the bracket ends; one
@@ -251,7 +251,12 @@ k_bisect(const BisectTask* __restrict__ tasks, const BisectItem* __restrict__ it
     lo = fmax(lo, glo);
     hi = fmin(hi, ghi);
   }
-  // Phase 1 (double-float): bisect until the bracket is below 2^-41 of the scale.
+  // Phase 1 (double-float): bisect until the bracket is below 2^-36 of the scale.  The
+  // FP64 phase starts with a secant step, whose error from the curvature of det(T - xI)
+  // is about width^2 / gap; at 2^-36 that stays far below the tolerance for relative
+  // gaps down to 1e-5 (a CPU emulation on n = 1024 minors and the batch families put
+  // every secant estimate inside its verification window), so narrowing further here
+  // would only add passes.
   {
     dflt dlo = df_of(lo), dhi = df_of(hi);
     bool act = active;
@@ -263,7 +268,7 @@ k_bisect(const BisectTask* __restrict__ tasks, const BisectItem* __restrict__ it
         mid.l *= 0.5f;
         if (sturm_count_df(dq, m, mid) > k) dhi = mid; else dlo = mid;
         const dflt w = df_add(dhi, {-dlo.h, -dlo.l});
-        act = (w.h > 0x1p-41f) && (++it1 < 64);
+        act = (w.h > 0x1p-36f) && (++it1 < 64);
       }
     }
     if (active) {
@@ -318,12 +323,15 @@ k_bisect(const BisectTask* __restrict__ tasks, const BisectItem* __restrict__ it
 
 }  // namespace
 
+static std::atomic<uint64_t> g_bisect_limit_set{0};
+
+cudaError_t preload_bisect() { return raise_smem_limit_once((const void*)k_bisect, g_bisect_limit_set); }
+
 cudaError_t launch_bisect(const BisectTask* tasks, const BisectItem* items, int nitems, int max_m,
                           unsigned* status, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
   const size_t smem = (size_t)max_m * (sizeof(double2) + sizeof(float4));
-  cudaError_t e = cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = raise_smem_limit_once((const void*)k_bisect, g_bisect_limit_set);
   if (e != cudaSuccess) return e;
   k_bisect<<<nitems, kBisectThreads, smem, s>>>(tasks, items, status);
   return cudaGetLastError();

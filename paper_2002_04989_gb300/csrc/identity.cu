@@ -119,12 +119,19 @@ k_identity(const IdentityProblem* __restrict__ probs, const IdentityItem* __rest
 
 }  // namespace
 
+static std::atomic<uint64_t> g_denom_limit_set{0}, g_identity_limit_set{0};
+
+cudaError_t preload_identity() {
+  cudaError_t e = raise_smem_limit_once((const void*)k_denominators, g_denom_limit_set);
+  if (e == cudaSuccess) e = raise_smem_limit_once((const void*)k_identity, g_identity_limit_set);
+  return e;
+}
+
 cudaError_t launch_denominators(const DenomTask* tasks, int ntasks, int max_n, unsigned* status,
                                 cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
   const size_t smem = (size_t)max_n * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_denominators,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit_once((const void*)k_denominators, g_denom_limit_set);
   if (e != cudaSuccess) return e;
   k_denominators<<<ntasks, 256, smem, s>>>(tasks, status);
   return cudaGetLastError();
@@ -134,8 +141,7 @@ cudaError_t launch_identity(const IdentityProblem* probs, const IdentityItem* it
                             int max_n, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
   const size_t smem = (size_t)(max_n > 1 ? max_n - 1 : 1) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_identity, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = raise_smem_limit_once((const void*)k_identity, g_identity_limit_set);
   if (e != cudaSuccess) return e;
   k_identity<<<nitems, kIdentityThreads, smem, s>>>(probs, items);
   return cudaGetLastError();

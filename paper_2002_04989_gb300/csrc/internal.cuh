@@ -1,10 +1,34 @@
 // Internal declarations shared by the eeid CUDA translation units.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace eeid {
+
+// Raise a kernel's dynamic shared memory limit to the device's opt-in maximum, once per
+// device (one bit of `done` per device).  The limit is only a ceiling, since every launch
+// passes its own size.  Changing it while launches of the kernel are queued makes the call
+// wait for them, which would serialise otherwise independent streams (two contexts, or
+// the serving loop's two batches).  So it is set once and never touched again.
+inline cudaError_t raise_smem_limit_once(const void* kernel, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 // Device status bits (OR-ed by kernels into a workspace word, read by eeid_sync).
 enum : unsigned {
@@ -98,6 +122,14 @@ struct IdentityItem {
 constexpr int kIdentityThreads = 128;
 cudaError_t launch_identity(const IdentityProblem* probs, const IdentityItem* items, int nitems,
                             int max_n, cudaStream_t s);
+
+// Load every kernel of a translation unit (and raise its shared memory limit) now.
+// With lazy module loading a kernel is otherwise loaded at its first launch, and a
+// load issued while other kernels run waits for them: the first batch of a serving
+// process would serialise behind whatever it overlaps.
+cudaError_t preload_tridiag();
+cudaError_t preload_bisect();
+cudaError_t preload_identity();
 
 // Deterministic symmetric matrix (uniform [-0.5, 0.5) entries) for the autotuner.
 cudaError_t launch_fill_symmetric(double* A, int n, int64_t lda, unsigned long long seed,

@@ -2,12 +2,15 @@
 //
 // Requests (a host matrix A and the component columns j wanted, rows = all i)
 // arrive on caller threads.  A scheduler thread admits them in arrival order while
-// the device budget allows, and merges every admitted request that is waiting into
-// one batched launch: all tridiagonalisations, bisections and identity evaluations
-// of the batch share the persistent kernels of eeid_components_batched.  Up to
-// `max_inflight` batches are on the GPU at once, each on its own stream with its
-// own context (workspace), so requests that arrive while a batch runs are launched
-// as soon as a slot and memory free up and their work overlaps the running batch.
+// the device budget allows, and merges the waiting requests of one cost band (see
+// cost_band) into one batched launch: all tridiagonalisations, bisections and
+// identity evaluations of the batch share the persistent kernels of
+// eeid_components_batched.  Up to `max_inflight` batches are on the GPU at once, each
+// on its own stream with its own context (workspace), so requests that arrive while
+// a batch runs are launched as soon as a slot and memory free up.  The contexts cut
+// each reduction into launches of one round of the grid, so the other batch's
+// kernels get SMs between them: a large request delays a small one by about one
+// round of its reductions, not by its whole run.
 // A request's matrix, output and eigenvalues stay resident on the device from
 // admission until its results are copied back.  Device buffers come from the
 // stream-ordered allocator; results go through pinned host buffers.
@@ -20,9 +23,11 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -31,6 +36,9 @@
 
 namespace eeid {
 void set_last_error(const char* msg);
+eeid_status set_round_launches(eeid_ctx* ctx, int enable);
+eeid_status set_sm_reserve(eeid_ctx* ctx, int sms);
+eeid_status reserve_workspace(eeid_ctx* ctx, size_t device_bytes, size_t staging_bytes);
 }
 
 namespace {
@@ -51,6 +59,7 @@ struct Request {
   double* h_out = nullptr;     // caller's result buffers (n x ncols, n)
   double* h_lambda = nullptr;
   char* pinned = nullptr;      // [A n*n | out n*ncols | lambda n] host staging
+  bool pooled = false;         // pinned comes from the server's pool (else cudaMallocHost)
   size_t bytes_a = 0, bytes_out = 0, bytes_lam = 0;
   size_t dev_bytes = 0;
   char* dev = nullptr;         // same layout on the device
@@ -58,6 +67,54 @@ struct Request {
   eeid_status status = EEID_OK;
   Clock::time_point t_submit, t_launch, t_done;
   int64_t batch_id = -1, batch_size = 0;
+};
+
+// The server's pinned staging pool: one page-locked region allocated at creation and
+// carved first-fit (256-byte granules, neighbours coalesced on release).  CUDA
+// serialises work of different streams around a page-locked allocation, so taking
+// request buffers from a pool keeps submits from stalling the batches in flight;
+// a request that does not fit falls back to its own allocation.  Guarded by the
+// server mutex.
+struct PinnedPool {
+  char* base = nullptr;
+  size_t size = 0;
+  std::map<size_t, size_t> free_;  // offset -> length
+
+  static size_t granule(size_t n) { return (n + 255) & ~(size_t)255; }
+  void init(char* b, size_t sz) {
+    base = b;
+    size = b ? sz : 0;
+    free_.clear();
+    if (size) free_[0] = size;
+  }
+  char* take(size_t n) {
+    n = granule(n);
+    for (auto it = free_.begin(); it != free_.end(); ++it)
+      if (it->second >= n) {
+        const size_t off = it->first, rest = it->second - n;
+        free_.erase(it);
+        if (rest) free_[off + n] = rest;
+        return base + off;
+      }
+    return nullptr;
+  }
+  void give(char* p, size_t n) {
+    n = granule(n);
+    size_t off = (size_t)(p - base);
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + n == next->first) {
+      n += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += n;
+        return;
+      }
+    }
+    free_[off] = n;
+  }
 };
 
 struct Slot {
@@ -73,6 +130,7 @@ struct Slot {
 
 struct eeid_server {
   int device = 0;
+  int sms = 1;
   size_t budget = 0;        // device bytes for resident requests
   size_t used = 0;
   int max_batch = 64;
@@ -88,12 +146,33 @@ struct eeid_server {
   int64_t next_batch = 0;
   int64_t batches_launched = 0;
   int64_t max_overlap = 0;  // most batches seen on the GPU at once
+  PinnedPool pool;
+  char* pool_mem = nullptr;
+  // The server's own stream-ordered device pool for request buffers: warmed to the
+  // request budget at creation and never trimmed, so no allocation maps new memory
+  // while batches run, and without cross-stream reuse dependencies, so one slot's
+  // allocation never waits for the other slot's frees.
+  cudaMemPool_t mempool = nullptr;
 };
 
 namespace {
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+size_t staging_bytes(const Request* r) { return r->bytes_a + r->bytes_out + r->bytes_lam; }
+
+// Return a request's staging buffer (the pool part under the server mutex).
+void release_staging(eeid_server* S, Request* r) {
+  if (!r->pinned) return;
+  if (r->pooled) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->pool.give(r->pinned, staging_bytes(r));
+  } else {
+    cudaFreeHost(r->pinned);
+  }
+  r->pinned = nullptr;
 }
 
 // Copy results to the callers' buffers, release device memory, mark done.
@@ -127,11 +206,33 @@ void finalize(eeid_server* S, Slot& sl, std::unique_lock<std::mutex>& lk, cudaEr
   S->cv_done.notify_all();
 }
 
-// Form a batch from the waiting requests that fit, upload, launch, download.
+// Cost band of a request: n^3 (columns + 1) is proportional to its Householder work
+// (the reductions dominate); everything below kTinyCost is one band, then a band per
+// factor of 8.  A batch holds requests of one band only, so a small request never
+// waits for the reductions of a much larger one that happens to be queued with it.
+constexpr double kTinyCost = 1e9;
+// Batches from this band up (about 0.2 s of reductions and more) leave 1/16 of the SMs
+// free of their persistent reduction CTAs, which take a whole SM each: a smaller batch
+// launched meanwhile runs there at once instead of waiting for round boundaries.
+constexpr int kReserveBand = 3;
+// Pinned staging pool for requests, and each slot's pinned metadata stage.
+constexpr size_t kPinnedPoolBytes = (size_t)1 << 30;
+constexpr size_t kStageBytes = (size_t)64 << 20;
+int cost_band(const Request* r) {
+  const double c = (double)r->n * r->n * r->n * (double)(r->ncols + 1);
+  if (c < kTinyCost) return 0;
+  return 1 + (int)(std::log2(c / kTinyCost) / 3.0);
+}
+
+// Form a batch from the waiting requests that fit, upload, launch, download.  The
+// batch is the longest run of waiting requests, in arrival order, that share the first
+// one's cost band and fit the device budget.
 bool launch(eeid_server* S, Slot& sl, std::unique_lock<std::mutex>& lk) {
   std::vector<Request*> batch;
+  int band = -1;
   while (!S->pending.empty() && (int)batch.size() < S->max_batch) {
     Request* r = S->pending.front();
+    if (!batch.empty() && cost_band(r) != band) break;
     if (S->used + r->dev_bytes > S->budget) {
       bool idle = batch.empty() && S->used == 0;
       if (idle) {  // can never fit
@@ -148,6 +249,7 @@ bool launch(eeid_server* S, Slot& sl, std::unique_lock<std::mutex>& lk) {
     S->pending.pop_front();
     S->used += r->dev_bytes;
     r->state = Request::RUNNING;
+    if (batch.empty()) band = cost_band(r);
     batch.push_back(r);
   }
   if (batch.empty()) return false;
@@ -172,7 +274,7 @@ bool launch(eeid_server* S, Slot& sl, std::unique_lock<std::mutex>& lk) {
   std::vector<eeid_problem> probs(batch.size());
   for (size_t q = 0; q < batch.size() && e == cudaSuccess; ++q) {
     Request* r = batch[q];
-    e = cudaMallocAsync((void**)&r->dev, r->dev_bytes, sl.stream);
+    e = cudaMallocFromPoolAsync((void**)&r->dev, r->dev_bytes, S->mempool, sl.stream);
     if (e != cudaSuccess) break;
     e = cudaMemcpyAsync(r->dev, r->pinned, r->bytes_a, cudaMemcpyHostToDevice, sl.stream);
     eeid_problem& p = probs[q];
@@ -187,7 +289,10 @@ bool launch(eeid_server* S, Slot& sl, std::unique_lock<std::mutex>& lk) {
     p.d_lambda = (double*)(r->dev + r->bytes_a + r->bytes_out);
   }
   eeid_status st = EEID_OK;
-  if (e == cudaSuccess) st = eeid_components_batched(sl.ctx, probs.data(), (int64_t)probs.size(), sl.stream);
+  if (e == cudaSuccess && S->slots.size() > 1)
+    st = eeid::set_sm_reserve(sl.ctx, band >= kReserveBand ? std::max(1, S->sms / 16) : 0);
+  if (e == cudaSuccess && st == EEID_OK)
+    st = eeid_components_batched(sl.ctx, probs.data(), (int64_t)probs.size(), sl.stream);
   if (e == cudaSuccess && st >= 0)
     for (Request* r : batch) {
       e = cudaMemcpyAsync(r->pinned + r->bytes_a, r->dev + r->bytes_a, r->bytes_out + r->bytes_lam,
@@ -247,6 +352,7 @@ eeid_status eeid_server_create(int device, const eeid_server_opts* opts, eeid_se
   cudaMemGetInfo(&fr, &tot);
   eeid_server* S = new eeid_server();
   S->device = device;
+  cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, device);
   const size_t total = (opts && opts->hbm_budget_bytes) ? opts->hbm_budget_bytes : fr / 2;
   const int inflight = (opts && opts->max_inflight > 0) ? opts->max_inflight : 2;
   S->max_batch = (opts && opts->max_batch > 0) ? opts->max_batch : 64;
@@ -258,6 +364,11 @@ eeid_status eeid_server_create(int device, const eeid_server_opts* opts, eeid_se
   for (auto& sl : S->slots) {
     eeid_status st = eeid_ctx_create(device, ws_budget, &sl.ctx);
     if (st == EEID_OK) st = eeid_set_graphs(sl.ctx, 0);
+    // reductions in round-sized launches: the other slot's kernels get SMs in between
+    if (st == EEID_OK) st = eeid::set_round_launches(sl.ctx, 1);
+    // the whole workspace and a metadata stage now, so no batch allocates later (an
+    // allocation would serialise the other slot's work with this one)
+    if (st == EEID_OK) st = eeid::reserve_workspace(sl.ctx, ws_budget, kStageBytes);
     if (st == EEID_OK) {
       e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
@@ -266,6 +377,32 @@ eeid_status eeid_server_create(int device, const eeid_server_opts* opts, eeid_se
     if (st != EEID_OK) {
       eeid_server_destroy(S);
       return st;
+    }
+  }
+  if (cudaMallocHost((void**)&S->pool_mem, kPinnedPoolBytes) != cudaSuccess) {
+    cudaGetLastError();   // no pool: every request allocates its own staging
+    S->pool_mem = nullptr;
+  }
+  S->pool.init(S->pool_mem, kPinnedPoolBytes);
+  {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    e = cudaMemPoolCreate(&S->mempool, &props);
+    uint64_t keep = UINT64_MAX;
+    int no = 0;
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(S->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e == cudaSuccess)
+      e = cudaMemPoolSetAttribute(S->mempool, cudaMemPoolReuseAllowInternalDependencies, &no);
+    void* warm = nullptr;
+    cudaStream_t s0 = S->slots[0].stream;
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&warm, S->budget, S->mempool, s0);
+    if (e == cudaSuccess) e = cudaFreeAsync(warm, s0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
+    if (e != cudaSuccess) {
+      eeid_server_destroy(S);
+      return sfail(EEID_ERR_NOMEM, std::string("device pool: ") + cudaGetErrorString(e));
     }
   }
   S->th = std::thread(scheduler, S);
@@ -289,7 +426,7 @@ void eeid_server_destroy(eeid_server* S) {
   S->cv_space.notify_all();
   if (S->th.joinable()) S->th.join();
   for (auto& kv : S->all) {
-    if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+    if (kv.second->pinned && !kv.second->pooled) cudaFreeHost(kv.second->pinned);
     delete kv.second;
   }
   for (auto& sl : S->slots) {
@@ -298,6 +435,8 @@ void eeid_server_destroy(eeid_server* S) {
     if (sl.stream) cudaStreamDestroy(sl.stream);
     if (sl.ctx) eeid_ctx_destroy(sl.ctx);
   }
+  if (S->pool_mem) cudaFreeHost(S->pool_mem);
+  if (S->mempool) cudaMemPoolDestroy(S->mempool);
   delete S;
 }
 
@@ -332,10 +471,18 @@ eeid_status eeid_server_submit(eeid_server* S, const double* hA, int64_t lda, in
     delete r;
     return sfail(EEID_ERR_NOMEM, "request larger than the server's device budget");
   }
-  cudaError_t e = cudaMallocHost((void**)&r->pinned, r->bytes_a + r->bytes_out + r->bytes_lam);
-  if (e != cudaSuccess) {
-    delete r;
-    return sfail(EEID_ERR_NOMEM, std::string("pinned staging: ") + cudaGetErrorString(e));
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->pinned = S->pool.take(staging_bytes(r));
+    r->pooled = r->pinned != nullptr;
+  }
+  if (!r->pinned) {
+    cudaError_t e = cudaMallocHost((void**)&r->pinned, staging_bytes(r));
+    if (e != cudaSuccess) {
+      r->pinned = nullptr;
+      delete r;
+      return sfail(EEID_ERR_NOMEM, std::string("pinned staging: ") + cudaGetErrorString(e));
+    }
   }
   double* pa = (double*)r->pinned;
   for (int64_t i = 0; i < n; ++i) memcpy(pa + i * n, hA + i * lda, sizeof(double) * n);
@@ -345,14 +492,14 @@ eeid_status eeid_server_submit(eeid_server* S, const double* hA, int64_t lda, in
     if ((int)S->pending.size() >= S->max_pending) {
       if (nonblocking) {
         lk.unlock();
-        cudaFreeHost(r->pinned);
+        release_staging(S, r);
         delete r;
         return sfail(EEID_ERR_BUSY, "server queue is full");
       }
       S->cv_space.wait(lk, [&] { return S->stop || (int)S->pending.size() < S->max_pending; });
       if (S->stop) {
         lk.unlock();
-        cudaFreeHost(r->pinned);
+        release_staging(S, r);
         delete r;
         return sfail(EEID_ERR_CANCELLED, "server is shutting down");
       }
@@ -388,7 +535,7 @@ eeid_status eeid_server_wait(eeid_server* S, uint64_t ticket, int64_t timeout_ms
   eeid_status st = r->state == Request::CANCELLED ? EEID_ERR_CANCELLED : r->status;
   S->all.erase(it);
   lk.unlock();
-  cudaFreeHost(r->pinned);
+  release_staging(S, r);
   delete r;
   if (st == EEID_ERR_CANCELLED) return sfail(st, "request cancelled before it ran");
   return st;

@@ -475,11 +475,17 @@ size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps) {
   return d * sizeof(double);
 }
 
+// One "limit raised" flag set per instantiation (see raise_smem_limit_once).
+template <bool SMEM, int W>
+std::atomic<uint64_t>& smem_limit_set() {
+  static std::atomic<uint64_t> done{0};
+  return done;
+}
+
 template <bool SMEM, int W>
 static cudaError_t launch_one(int grid, const TridiagLaunch& L, cudaStream_t s) {
   const size_t smem = tridiag_smem_bytes(SMEM, L.max_m, W);
-  cudaError_t e = cudaFuncSetAttribute(k_tridiag<SMEM, W>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit_once((const void*)k_tridiag<SMEM, W>, smem_limit_set<SMEM, W>());
   if (e != cudaSuccess) return e;
   k_tridiag<SMEM, W><<<grid, W * 32, smem, s>>>(L);
   return cudaGetLastError();
@@ -507,15 +513,25 @@ cudaError_t launch_tridiag(bool smem_path, int warps, int grid, const TridiagLau
 }
 
 // Occupancy query used by the planner to size persistent grids.
+cudaError_t preload_tridiag() {
+  cudaError_t e = cudaSuccess;
+#define EEID_PRE(S_, W_) \
+  if (e == cudaSuccess) e = raise_smem_limit_once((const void*)k_tridiag<S_, W_>, smem_limit_set<S_, W_>());
+  EEID_PRE(true, 1) EEID_PRE(true, 2) EEID_PRE(true, 4) EEID_PRE(true, 8)
+  EEID_PRE(false, 2) EEID_PRE(false, 4) EEID_PRE(false, 8) EEID_PRE(false, 12) EEID_PRE(false, 16)
+#undef EEID_PRE
+  return e;
+}
+
 int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m) {
   const size_t smem = tridiag_smem_bytes(smem_path, max_m, warps);
   int nb = 0;
   cudaError_t e = cudaErrorInvalidValue;
 #define EEID_OCC(S_, W_)                                                                   \
   if (smem_path == S_ && warps == W_) {                                                    \
-    cudaFuncSetAttribute(k_tridiag<S_, W_>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                         (int)smem);                                                       \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tridiag<S_, W_>, W_ * 32, smem); \
+    e = raise_smem_limit_once((const void*)k_tridiag<S_, W_>, smem_limit_set<S_, W_>());    \
+    if (e == cudaSuccess)                                                                  \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tridiag<S_, W_>, W_ * 32, smem); \
   }
   EEID_OCC(true, 1) EEID_OCC(true, 2) EEID_OCC(true, 4) EEID_OCC(true, 8)
   EEID_OCC(false, 2) EEID_OCC(false, 4) EEID_OCC(false, 8) EEID_OCC(false, 12) EEID_OCC(false, 16)

@@ -81,6 +81,28 @@ def test_arrivals_overlap_a_running_batch(torch_cuda):
         assert np.array_equal(out, o_ref)
 
 
+def test_cost_bands_and_round_launches(torch_cuda):
+    """A large request and small ones queued at the same moment go to different batches
+    (cost bands), and the small ones finish first although the large batch was
+    launched first: its reductions run one round at a time, so the second slot's
+    kernels get SMs in between."""
+    big = inputs.planted(1200, 9, gap=1e-4).A
+    smalls = [inputs.goe(30 + 7 * k, 90 + k) for k in range(3)]
+    with eeid.Server(0, max_batch=16, max_inflight=2) as srv:
+        tb = srv.eeid_server_submit(big)
+        ts = [srv.eeid_server_submit(A) for A in smalls]
+        small_res = [srv.eeid_server_wait(t) for t in ts]
+        t_small_done = time.perf_counter()
+        big_res = srv.eeid_server_wait(tb)
+        t_big_done = time.perf_counter()
+    assert all(r[2]["batch_id"] != big_res[2]["batch_id"] for r in small_res)
+    assert t_small_done < t_big_done
+    assert max(r[2]["total_ms"] for r in small_res) < 0.5 * big_res[2]["total_ms"]
+    for A, (out, lam, st) in zip(smalls, small_res):
+        o_ref, _ = solo(torch_cuda, A)
+        assert np.array_equal(out, o_ref)
+
+
 def test_cancel_and_bounded_wait(torch_cuda):
     big = inputs.planted(1200, 6, gap=1e-4).A
     small = inputs.goe(30, 3)
