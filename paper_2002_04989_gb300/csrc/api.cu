@@ -4,6 +4,7 @@
 //   (minors, interlacing brackets) -> K-c identity.
 // Every arithmetic step runs in the CUDA kernels; the host only plans and launches.
 #include "eeid.h"
+#include "host_plan.h"
 #include "internal.cuh"
 
 #include <algorithm>
@@ -266,11 +267,7 @@ bool rule_covers(const eeid_ctx* ctx, int m) {
   return false;
 }
 
-// Time of one round of the 8-warp global variant at two CTAs per SM (twice the
-// matrices) over one round of the 16-warp variant at one CTA per SM, measured on
-// GB300 at m = 1023 (the second warp group's reduction and reflector phases overlap
-// the first's tile pass, so the FP64 pipe stays busier).
-constexpr double kRound8x2Per16 = 1.89;
+
 
 int blocks_per_sm(eeid_ctx* ctx, const TriCfg& c, int max_m) {
   int& cache = ctx->occ_cache[c.smem ? 0 : 1][c.warps];
@@ -395,12 +392,6 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     GroupPlan& g = gplans[0];
     const int nt = (int)g.idx.size();
     const bool uniform = tri[g.idx.back()].m + 1 >= tri[g.idx.front()].m;
-    // every A must be done before the minors' brackets are set
-    auto a_from = [&](int q0) {
-      for (int q = std::max(0, q0); q < nt; ++q)
-        if (tri[g.idx[q]].col < 0) return true;
-      return false;
-    };
     auto split_at = [&](int at, int grid) {
       tail_at = at;
       tail_grid = grid;
@@ -408,31 +399,20 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
       counter2_off = meta.take(sizeof(int));
       for (int q = at; q < nt; ++q) in_tail[g.idx[q]] = 1;
     };
-    bool hybrid = false;
+    int last_a = -1;
+    for (int q = 0; q < nt; ++q)
+      if (tri[g.idx[q]].col < 0) last_a = q;
     const TriCfg c8{false, 8};
-    if (uniform && !g.cfg.smem && g.cfg.warps >= 12 && !rule_covers(ctx, g.max_m) &&
-        cfg_supported(false, 8, g.max_m)) {
-      const int b8 = blocks_per_sm(ctx, c8, g.max_m);
-      const int G8 = ctx->sms * b8, G16 = g.grid;
-      const int bulk = nt / G8 * G8, r = nt - bulk;
-      const double t_hybrid = (double)(bulk / G8) * kRound8x2Per16 + (r > 0 ? 1.0 : 0.0);
-      const double t_plain = (double)((nt + G16 - 1) / G16);
-      if (b8 >= 2 && G16 == ctx->sms && bulk > 0 && r <= G16 && t_hybrid < t_plain &&
-          !a_from(bulk)) {
-        hybrid = true;
-        tail_cfg = g.cfg;
-        g.cfg = c8;
-        g.grid = G8;
-        if (r > 0) split_at(bulk, r);
-      }
+    const bool wide = !g.cfg.smem && g.cfg.warps >= 12;
+    const int blocks8 = (wide && !rule_covers(ctx, g.max_m) && cfg_supported(false, 8, g.max_m))
+                            ? blocks_per_sm(ctx, c8, g.max_m) : 0;
+    const RoundPlan rp = plan_rounds(nt, g.grid, ctx->sms, wide, blocks8, uniform, last_a);
+    tail_cfg = g.cfg;   // the tail runs the group's default variant
+    if (rp.hybrid) {
+      g.cfg = c8;
+      g.grid = rp.bulk_grid;
     }
-    if (!hybrid) {
-      const int G = g.grid, r = nt % G;
-      if (nt > G && r > 0 && G - r >= std::max(1, G / 16) && uniform && !a_from(nt - r)) {
-        tail_cfg = g.cfg;
-        split_at(nt - r, r);
-      }
-    }
+    if (rp.tail_at > 0) split_at(rp.tail_at, rp.tail_grid);
   }
   // bisection tasks: A's first (their eigenvalues seed the minors' brackets); with the
   // tail overlap the minors of the tail are bisected in a second launch

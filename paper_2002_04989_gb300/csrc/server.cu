@@ -18,6 +18,7 @@
 // Every kernel a batch runs depends only on the sizes of its own matrices, so a
 // request's result is bitwise the same alone and in any mix.
 #include "eeid.h"
+#include "host_plan.h"
 
 #include <cuda_runtime.h>
 
@@ -69,54 +70,6 @@ struct Request {
   int64_t batch_id = -1, batch_size = 0;
 };
 
-// The server's pinned staging pool: one page-locked region allocated at creation and
-// carved first-fit (256-byte granules, neighbours coalesced on release).  CUDA
-// serialises work of different streams around a page-locked allocation, so taking
-// request buffers from a pool keeps submits from stalling the batches in flight;
-// a request that does not fit falls back to its own allocation.  Guarded by the
-// server mutex.
-struct PinnedPool {
-  char* base = nullptr;
-  size_t size = 0;
-  std::map<size_t, size_t> free_;  // offset -> length
-
-  static size_t granule(size_t n) { return (n + 255) & ~(size_t)255; }
-  void init(char* b, size_t sz) {
-    base = b;
-    size = b ? sz : 0;
-    free_.clear();
-    if (size) free_[0] = size;
-  }
-  char* take(size_t n) {
-    n = granule(n);
-    for (auto it = free_.begin(); it != free_.end(); ++it)
-      if (it->second >= n) {
-        const size_t off = it->first, rest = it->second - n;
-        free_.erase(it);
-        if (rest) free_[off + n] = rest;
-        return base + off;
-      }
-    return nullptr;
-  }
-  void give(char* p, size_t n) {
-    n = granule(n);
-    size_t off = (size_t)(p - base);
-    auto next = free_.lower_bound(off);
-    if (next != free_.end() && off + n == next->first) {
-      n += next->second;
-      next = free_.erase(next);
-    }
-    if (next != free_.begin()) {
-      auto prev = std::prev(next);
-      if (prev->first + prev->second == off) {
-        prev->second += n;
-        return;
-      }
-    }
-    free_[off] = n;
-  }
-};
-
 struct Slot {
   eeid_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
@@ -146,7 +99,7 @@ struct eeid_server {
   int64_t next_batch = 0;
   int64_t batches_launched = 0;
   int64_t max_overlap = 0;  // most batches seen on the GPU at once
-  PinnedPool pool;
+  eeid::PinnedPool pool;   // pinned staging (see host_plan.h), guarded by mu
   char* pool_mem = nullptr;
   // The server's own stream-ordered device pool for request buffers: warmed to the
   // request budget at creation and never trimmed, so no allocation maps new memory
@@ -206,11 +159,6 @@ void finalize(eeid_server* S, Slot& sl, std::unique_lock<std::mutex>& lk, cudaEr
   S->cv_done.notify_all();
 }
 
-// Cost band of a request: n^3 (columns + 1) is proportional to its Householder work
-// (the reductions dominate); everything below kTinyCost is one band, then a band per
-// factor of 8.  A batch holds requests of one band only, so a small request never
-// waits for the reductions of a much larger one that happens to be queued with it.
-constexpr double kTinyCost = 1e9;
 // Batches from this band up (about 0.2 s of reductions and more) leave 1/16 of the SMs
 // free of their persistent reduction CTAs, which take a whole SM each: a smaller batch
 // launched meanwhile runs there at once instead of waiting for round boundaries.
@@ -218,11 +166,9 @@ constexpr int kReserveBand = 3;
 // Pinned staging pool for requests, and each slot's pinned metadata stage.
 constexpr size_t kPinnedPoolBytes = (size_t)1 << 30;
 constexpr size_t kStageBytes = (size_t)64 << 20;
-int cost_band(const Request* r) {
-  const double c = (double)r->n * r->n * r->n * (double)(r->ncols + 1);
-  if (c < kTinyCost) return 0;
-  return 1 + (int)(std::log2(c / kTinyCost) / 3.0);
-}
+// A batch holds requests of one cost band only (eeid::cost_band), so a small request
+// never waits for the reductions of a much larger one that happens to be queued with it.
+int cost_band(const Request* r) { return eeid::cost_band(r->n, r->ncols); }
 
 // Form a batch from the waiting requests that fit, upload, launch, download.  The
 // batch is the longest run of waiting requests, in arrival order, that share the first

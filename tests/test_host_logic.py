@@ -1,0 +1,159 @@
+"""Host-side planning rules of the CUDA path (csrc/host_plan.h), compiled with the host
+C++ compiler and checked on the CPU: how a group of near-equal Householder reductions is
+split into launches (hybrid rounds, tail overlap), the serving cost bands, and the
+serving loop's pinned staging allocator."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2002_04989_gb300", "csrc")
+
+DRIVER = r"""
+#include "host_plan.h"
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include <random>
+using namespace eeid;
+int main(int argc, char** argv) {
+  if (!strcmp(argv[1], "plan")) {
+    // nt grid sms wide blocks8 uniform last_a
+    int a[7];
+    for (int i = 0; i < 7; ++i) a[i] = atoi(argv[2 + i]);
+    RoundPlan p = plan_rounds(a[0], a[1], a[2], a[3] != 0, a[4], a[5] != 0, a[6]);
+    printf("%d %d %d %d\n", p.hybrid ? 1 : 0, p.bulk_grid, p.tail_at, p.tail_grid);
+  } else if (!strcmp(argv[1], "band")) {
+    printf("%d\n", cost_band(atoll(argv[2]), atoll(argv[3])));
+  } else if (!strcmp(argv[1], "pool")) {
+    const size_t size = (size_t)1 << 24;
+    std::vector<char> mem(size);
+    PinnedPool pool;
+    pool.init(mem.data(), size);
+    std::mt19937_64 rng(atoi(argv[2]));
+    struct Blk { char* p; size_t n; };
+    std::vector<Blk> live;
+    long takes = 0, fails = 0;
+    for (int step = 0; step < 20000; ++step) {
+      if (live.empty() || rng() % 3) {
+        size_t n = 1 + rng() % 200000;
+        char* p = pool.take(n);
+        if (!p) { ++fails; continue; }
+        ++takes;
+        // inside the region, 256-byte aligned offset, no overlap with a live block
+        if (p < mem.data() || p + n > mem.data() + size || (p - mem.data()) % 256) { printf("BAD range\n"); return 1; }
+        for (auto& b : live)
+          if (p < b.p + PinnedPool::granule(b.n) && b.p < p + PinnedPool::granule(n)) { printf("BAD overlap\n"); return 1; }
+        live.push_back({p, n});
+      } else {
+        size_t i = rng() % live.size();
+        pool.give(live[i].p, live[i].n);
+        live.erase(live.begin() + i);
+      }
+      // free list: sorted, disjoint, no two adjacent blocks left uncoalesced
+      size_t end = 0; bool first = true;
+      for (auto& kv : pool.free_) {
+        if (!first && kv.first <= end) { printf("BAD free list %zu %zu\n", kv.first, end); return 1; }
+        end = kv.first + kv.second; first = false;
+      }
+    }
+    for (auto& b : live) pool.give(b.p, b.n);
+    printf("%ld %ld %zu %zu %zu\n", takes, fails, pool.free_.size(),
+           pool.free_.empty() ? (size_t)0 : pool.free_.begin()->first,
+           pool.free_.empty() ? (size_t)0 : pool.free_.begin()->second);
+  }
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def driver(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    d = tmp_path_factory.mktemp("host_plan")
+    src = d / "driver.cpp"
+    src.write_text(DRIVER)
+    exe = d / "driver"
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+
+    def run(*args):
+        out = subprocess.run([str(exe), *map(str, args)], capture_output=True, text=True, check=True)
+        return out.stdout.split()
+    return run
+
+
+def plan(driver, nt, grid=152, sms=152, wide=1, blocks8=2, uniform=1, last_a=0):
+    h, bulk, at, tg = map(int, driver("plan", nt, grid, sms, wide, blocks8, uniform, last_a))
+    return bool(h), bulk, at, tg
+
+
+def test_plan_benchmark_sizes(driver):
+    # n = 1024, all columns: 1025 reductions -> three 8-warp pair-rounds + a 113-task tail
+    assert plan(driver, 1025) == (True, 304, 912, 113)
+    # 304 tasks: one pair-round beats two 16-warp rounds, nothing left for a tail
+    assert plan(driver, 304) == (True, 304, 0, 0)
+    # n = 4096 (the 8-warp variant does not fit twice per SM): 257 tasks, 105-task tail
+    assert plan(driver, 257, blocks8=1) == (False, 152, 152, 105)
+    # n = 520: remainder of the pair-rounds (217) exceeds one round -> plain tail of 65
+    assert plan(driver, 521) == (False, 152, 456, 65)
+    # exactly one round: nothing to split
+    assert plan(driver, 152) == (False, 152, 0, 0)
+
+
+def test_plan_refusals(driver):
+    # sizes not within 1 of each other: no split at all
+    assert plan(driver, 1025, uniform=0) == (False, 152, 0, 0)
+    # an A among the last tasks: its eigenvalues must come from the first launch
+    assert plan(driver, 1025, last_a=1000) == (False, 152, 0, 0)
+    # a last round that leaves fewer than 1/16 of the SMs idle is not worth a second launch
+    assert plan(driver, 600, blocks8=0) == (False, 152, 0, 0)
+    # a narrow default (4-warp variant at several CTAs per SM) is never replaced
+    assert plan(driver, 1025, grid=608, wide=0)[0] is False
+    # a budget-shrunk grid (fewer CTAs than SMs) does not use pair-rounds
+    assert plan(driver, 1025, grid=100)[0] is False
+
+
+def test_plan_invariants(driver):
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        sms = int(rng.integers(8, 200))
+        grid = sms
+        nt = int(rng.integers(1, 6 * sms))
+        blocks8 = int(rng.integers(0, 3))
+        last_a = int(rng.integers(0, nt))
+        h, bulk, at, tg = plan(driver, nt, grid, sms, 1, blocks8, 1, last_a)
+        assert 0 <= at < nt or at == 0
+        if at:
+            assert last_a < at                       # every A in the first launch
+            assert 0 < tg <= grid and tg == nt - at  # the tail is at most one round
+            assert grid - tg >= max(1, grid // 16) or h
+        if h:
+            assert blocks8 >= 2 and bulk == sms * blocks8
+            assert at == 0 or at % bulk == 0         # the first launch is whole pair-rounds
+
+
+def test_cost_bands(driver):
+    band = lambda n, c: int(driver("band", n, c)[0])
+    assert band(16, 1) == 0 and band(100, 100) == 0            # below 1e9: one band
+    assert band(2048, 2048) == 5                               # 2048^3 * 2049 ~ 1.8e13
+    assert band(1200, 1200) == 4
+    costs = sorted((n ** 3 * (c + 1), n, c) for n in (16, 64, 200, 500, 1000, 2048)
+                   for c in (1, 8, 64, n))
+    bands = [band(n, c) for _, n, c in costs]
+    assert bands == sorted(bands)                              # monotone in the cost
+    # n = 1000 gives n^3 = 1e9: bands change where (columns + 1) crosses a power of 8
+    assert [band(1000, c) for c in (0, 6, 7, 62, 63)] == [1, 1, 2, 2, 3]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_pinned_pool(driver, seed):
+    takes, fails, nfree, off, length = map(int, driver("pool", seed))
+    assert takes > 5000
+    # everything given back coalesces into the one region it started as
+    assert (nfree, off, length) == (1, 0, 1 << 24)
