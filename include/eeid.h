@@ -142,14 +142,16 @@ eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* probs, in
  * directly (better when batch shapes never repeat, as in serving). */
 eeid_status eeid_set_graphs(eeid_ctx* ctx, int enable);
 
-/* Enable (default) or disable the tail overlap.  When one call's Householder
- * reductions (A and its minors, Sec. 2) are near-equal in size and take more than
- * one round of the persistent grid, the last, partial round is launched on an
- * internal greatest-priority stream. Meanwhile the caller's stream bisects the
- * eigenvalues of A and of the minors already reduced, on the SMs that round leaves
- * idle.  The two streams join before the last minors' bisection, so the call still
- * completes in the caller's stream order.  Results are bitwise the same either way;
- * with the overlap on, the phase times of eeid_phase_times may overlap. */
+/* Enable (default) or disable the round plan of large calls.  When one call's
+ * Householder reductions (A and its minors, Sec. 2) are near-equal in size and take
+ * more than one round of the persistent grid, whole rounds may run as two 8-warp CTAs
+ * per SM (hybrid rounds, when the size allows two per SM), and the last, partial
+ * round is launched on an internal greatest-priority stream.  Meanwhile the caller's
+ * stream bisects the eigenvalues of A and of the minors already reduced, on the SMs
+ * that round leaves idle.  The two streams join before the last minors' bisection,
+ * so the call still completes in the caller's stream order.  Results are bitwise the
+ * same either way; with the plan on, the phase times of eeid_phase_times may
+ * overlap. */
 eeid_status eeid_set_overlap(eeid_ctx* ctx, int enable);
 
 /* Number of kernel launches the context has enqueued so far (for accounting). */
@@ -159,9 +161,12 @@ int64_t eeid_launch_count(const eeid_ctx* ctx);
  * reduced by the variant `path` (0 = working matrix resident in shared memory,
  * m <= 160; 1 = working matrix in a global-memory slot per CTA) with `warps` warps
  * per CTA (path 0: 1, 2, 4, 8; path 1: 2, 4, 8, 12, 16).  Later rules take precedence.
- * Results are bitwise reproducible for a fixed rule set; changing the variant of a
- * size changes the rounding order (not the accuracy class).  EEID_ERR_INVALID for
- * an unsupported combination. */
+ * The warp count never changes a result: every instantiation of one path sums in
+ * the same order, so the two paths' results are each bitwise fixed by m.  Changing
+ * the path of a size changes the rounding order (not the accuracy class).  A rule
+ * covering a size also keeps calls from switching it to the 8-warp two-CTAs-per-SM
+ * rounds that are otherwise used for large near-equal groups (see eeid_set_overlap).
+ * EEID_ERR_INVALID for an unsupported combination. */
 eeid_status eeid_tune_tridiag(eeid_ctx* ctx, int m_lo, int m_hi, int path, int warps);
 
 /* Drop all tuning rules (back to the built-in size table). */
