@@ -216,7 +216,7 @@ int eeid_phase_times(eeid_ctx* ctx, double* ms, int cap);
  * by about one round, not its whole run.  A request's matrix, output and eigenvalues stay
  * resident on the device until its results are copied back.  Each result is
  * bitwise the same as eeid_components on that matrix alone.  (The paper serves one
- * component per call; this is the build's own serving form of Eq. 1.) */
+ * component per call; this request loop is the library's own serving form of Eq. 1.) */
 typedef struct eeid_server eeid_server;
 
 typedef struct {
