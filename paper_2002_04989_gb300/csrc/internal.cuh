@@ -16,7 +16,8 @@ inline cudaError_t raise_smem_limit_once(const void* kernel, std::atomic<uint64_
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const uint64_t bit = 1ull << (dev & 63);
+  // devices 0..63 are remembered; a higher index is simply set again each time
+  const uint64_t bit = dev < 64 ? 1ull << dev : 0;
   if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
