@@ -51,3 +51,34 @@ def test_reference_leg_nonzero_rank_exits_clean(capsys):
     finally:
         os.environ.pop("RANK")
     assert capsys.readouterr().out == ""
+
+
+def test_reference_line_contract(capsys, monkeypatch):
+    """The reference arm's JSON line: the oracle as the baseline program, the bench's
+    metric, unit and direction, and an e2e object with no device copies."""
+    import json
+
+    import bench
+    monkeypatch.setattr(bench, "oracle_sample", lambda p, target_s=15.0: (2300.0, 32, 14.0, 16))
+    assert bench.run_reference(bench.argparse.Namespace(steps=2, warmup=3), 1, 0) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == bench.UNIT and line["higher_is_better"] is True
+    assert line["value"] == 2300.0 and line["steps"] == 2 and line["warmup"] == 3
+    assert line["vs_baseline"] is None and line["dtype"] == "f64" and line["n_gpus"] == 1
+    assert line["config"]["workload"] == bench.WORKLOAD
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] == 16
+    assert "columns" in cb["sample"]
+    assert line["e2e"] == {"value": 2300.0, "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_oracle_sample_runs_bounded():
+    """The oracle timing leg on a short budget: whole columns of the n = 1024 planted
+    matrix, a positive rate, the cores it used."""
+    import bench
+    from paper_2002_04989_gb300 import inputs
+    v, cols, dt, cores = bench.oracle_sample(inputs.planted1024(), target_s=0.3)
+    assert v > 0 and 1 <= cols <= 1023 and dt > 0 and cores >= 1
+    assert abs(v - 1024 * cols / dt) <= 1e-6 * v
