@@ -243,7 +243,12 @@ typedef struct {
   int64_t device_budget_bytes;
 } eeid_server_info_t;
 
-/* Start a server on `device` (opts may be NULL for defaults). */
+/* Start a server on `device` (opts may be NULL for defaults).  The whole device
+ * budget is taken here, not on demand: each batch workspace is allocated in full and
+ * the request half warms a stream-ordered pool of the server's own.  A 1 GiB pinned
+ * host pool for request staging is allocated too.  Nothing then allocates while batches
+ * run, since an allocation would serialise the two batches' streams.  Errors:
+ * EEID_ERR_INVALID, EEID_ERR_CUDA, EEID_ERR_NOMEM (the budget cannot be allocated). */
 eeid_status eeid_server_create(int device, const eeid_server_opts* opts, eeid_server** out);
 
 /* Stop: cancels requests not yet admitted, waits for the batches on the GPU, frees
