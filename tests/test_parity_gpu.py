@@ -204,6 +204,17 @@ def test_argument_errors(torch_cuda, ctx):
         assert ei.value.status == eeid.EEID_ERR_INVALID
 
 
+def test_size_limit_refused(torch_cuda, ctx):
+    """n above the kernels' limit (4096) is refused on the host, before anything is
+    queued; n = 4096 itself is the planted4096 workload (test_workloads_gpu)."""
+    from paper_2002_04989_gb300 import eeid
+    A = torch_cuda.zeros((4097, 4097), dtype=torch_cuda.float64, device="cuda")
+    with pytest.raises(eeid.EeidError) as ei:
+        ctx.eeid_components(A, rows=[0], cols=[0])
+    assert ei.value.status == eeid.EEID_ERR_INVALID
+    del A
+
+
 def test_degenerate_warns_and_nans(torch_cuda, ctx):
     from paper_2002_04989_gb300 import eeid
     A = np.diag([1.0, 2.0, 2.0, 3.0])
