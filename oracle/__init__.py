@@ -118,14 +118,29 @@ def eig_vsq(A):
     return lam, vsq
 
 
-def eigvecs(A):
-    """(lam, vec) with vec[i, j] = component j of the unit eigenvector i (signed)."""
+def eigvecs(A, convention=False):
+    """(lam, vec) with vec[i, j] = component j of the unit eigenvector i (signed),
+    from cyclic Jacobi with the rotations accumulated.  Each eigenvector is defined
+    up to its sign; with ``convention`` the sign is fixed by ``sign_convention``."""
     A = _mat(A)
     n = A.shape[0]
     lam = np.empty(n)
     vec = np.empty((n, n))
     _check(_load().oracle_eigvecs(n, _d(A), n, _d(lam), _d(vec)), "oracle_eigvecs")
-    return lam, vec
+    return lam, (sign_convention(vec) if convention else vec)
+
+
+def sign_convention(vec):
+    """The sign convention for signed eigenvectors (rows of ``vec``): the component of
+    largest magnitude is made positive (the first such component on exact ties).
+    Eq. 1 (Sec. 2) fixes only |v_ij|, so any signed result is compared in this form."""
+    vec = np.array(vec, dtype=np.float64, copy=True)
+    if vec.size == 0:
+        return vec
+    jstar = np.argmax(np.abs(vec), axis=1)
+    flip = vec[np.arange(vec.shape[0]), jstar] < 0
+    vec[flip] *= -1.0
+    return vec
 
 
 def minor_eigvals(A, cols=None):

@@ -14,6 +14,10 @@
  *                                     "Matrix Computations", sec. 8.5) -- the
  *                                     plain definition of the spectrum and of the
  *                                     unit eigenvectors of a symmetric A (Sec. 2).
+ *   oracle_eigvecs                    the same Jacobi run's unit eigenvectors
+ *                                     themselves, signed (each is defined up to its
+ *                                     sign; tests fix it by the convention that the
+ *                                     largest-magnitude component is positive).
  *   oracle_minor_eigvals              the same Jacobi on the minor M_j, i.e. A with
  *                                     row and column j removed (Sec. 2, definition
  *                                     under Eq. 1).

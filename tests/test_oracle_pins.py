@@ -8,7 +8,10 @@ not against the oracle itself.  CPU only.
 * invariants of any orthonormal eigenbasis and Cauchy interlacing;
 * brute force: eigenvectors by shifted inverse iteration for n <= 8;
 * a library routine: LAPACK's symmetric eigensolver through numpy;
-* a planted spectrum with known eigenvectors Q.
+* a planted spectrum with known eigenvectors Q;
+* the signed eigenvectors (oracle.eigvecs): the 2x2 eigenvector (b, lam - a), the
+  Toeplitz sine vectors, the residual A v = lam v with V^T V = I, inverse iteration,
+  planted Q, and the sign convention (largest-magnitude component positive).
 A last group plants plausible mistakes (dropped factor, swapped numerator and
 denominator, i and j exchanged, wrong minor) into the oracle's inputs and shows
 that the pins reject each of them.
@@ -234,3 +237,101 @@ def test_pins_reject_planted_mistakes(oracle_mod):
     lam_bad = lam.copy()
     lam_bad[0] = -lam_bad[0]
     assert rejected(oracle_mod.identity(np.sort(lam_bad), mu))
+
+
+# ------------------------------------------------------------------ signed eigenvectors
+# oracle.eigvecs returns the Jacobi eigenvectors themselves (signed), the oracle for
+# signed components.  Each pin below is independent of the oracle's own code: a closed
+# form, a defining equation, or brute force.  Vectors are compared up to one sign per
+# eigenvector; the convention (largest-magnitude component positive) is pinned too.
+
+def same_up_to_sign(a, b):
+    """max over rows of min(|a_i - b_i|, |a_i + b_i|) (elementwise max)."""
+    d1 = np.max(np.abs(a - b), axis=1)
+    d2 = np.max(np.abs(a + b), axis=1)
+    return float(np.max(np.minimum(d1, d2))) if a.size else 0.0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_eigvecs_2x2_closed_form(oracle_mod, seed):
+    g = np.random.default_rng(200 + seed)
+    a, b, c = g.standard_normal(3)
+    A = np.array([[a, b], [b, c]])
+    h = math.sqrt(((a - c) / 2) ** 2 + b * b)
+    lam_c = [(a + c) / 2 - h, (a + c) / 2 + h]
+    # row 0 of (A - lam I) x = 0 gives x = (b, lam - a) for either eigenvalue
+    expect = np.array([[b, l - a] for l in lam_c])
+    expect /= np.linalg.norm(expect, axis=1)[:, None]
+    lam, vec = oracle_mod.eigvecs(A)
+    assert np.max(np.abs(lam - lam_c)) < 4e-16 * (abs(a) + abs(b) + abs(c) + 1)
+    assert same_up_to_sign(vec, expect) < 1e-14
+
+
+@pytest.mark.parametrize("n,a,b", [(3, 0.25, -0.5), (8, 0.0, 1.0), (17, -1.0, 0.75), (32, 0.0, 1.0)])
+def test_eigvecs_toeplitz_sine_vectors(oracle_mod, n, a, b):
+    """Tridiagonal Toeplitz: eigenvalue a + 2b cos(k pi/(n+1)) has the eigenvector
+    sqrt(2/(n+1)) sin(j k pi/(n+1)), j = 1..n (1-based)."""
+    A = inputs.toeplitz(n, a, b)
+    k = np.arange(1, n + 1)
+    lam_k = a + 2 * b * np.cos(k * np.pi / (n + 1))
+    order = np.argsort(lam_k)                       # ascending relabelling
+    j = np.arange(1, n + 1)
+    vec_c = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(k[order], j) * np.pi / (n + 1))
+    lam, vec = oracle_mod.eigvecs(A)
+    assert np.max(np.abs(lam - lam_k[order])) < 1e-14
+    assert same_up_to_sign(vec, vec_c) < 1e-13
+
+
+@pytest.mark.parametrize("kind,n", [("goe", 9), ("goe", 40), ("wishart", 24), ("planted", 30)])
+def test_eigvecs_residual_and_orthonormality(oracle_mod, kind, n):
+    """A v_i = lam_i v_i (row i of vec) and V^T V = I: the definition of an
+    orthonormal eigenbasis of a symmetric A."""
+    A = (inputs.goe(n, 17) if kind == "goe" else inputs.wishart(n, 18) if kind == "wishart"
+         else inputs.planted(n, 19, gap=1e-2).A)
+    lam, vec = oracle_mod.eigvecs(A)
+    norm = max(abs(lam[0]), abs(lam[-1]))
+    resid = A @ vec.T - vec.T * lam[None, :]
+    assert np.max(np.abs(resid)) < 1e-14 * n * norm
+    assert np.max(np.abs(vec @ vec.T - np.eye(n))) < 1e-14 * n
+    # the squared components are the oracle's |v_ij|^2 grid (both from one Jacobi run)
+    _, vsq = oracle_mod.eig_vsq(A)
+    assert np.max(np.abs(vec * vec - vsq)) < 1e-16 * n
+
+
+@pytest.mark.parametrize("n", [3, 5, 8])
+def test_eigvecs_inverse_iteration_brute_force(oracle_mod, n):
+    A = inputs.goe(n, 40 + n)
+    lam, vec = oracle_mod.eigvecs(A)
+    for i in range(n):
+        x = oracle_mod.inverse_iteration(A, lam[i] + 1e-9 * (1 + abs(lam[i])), iters=4)
+        assert same_up_to_sign(vec[i:i + 1], x[None, :]) < 1e-14
+
+
+def test_eigvecs_planted_q(oracle_mod):
+    p = inputs.planted(40, 21, -1.0, 1.0, 1e-2)
+    lam, vec = oracle_mod.eigvecs(p.A)
+    assert np.max(np.abs(lam - p.lam)) < 1e-14
+    assert same_up_to_sign(vec, p.Q.T) < 1e-12
+
+
+def test_sign_convention():
+    vec = np.array([[0.6, -0.8], [-0.8, -0.6], [0.0, 0.0]])
+    import oracle
+    out = oracle.sign_convention(vec)
+    assert np.array_equal(out, [[-0.6, 0.8], [0.8, 0.6], [0.0, 0.0]])
+    # ties: the first largest component decides
+    t = oracle.sign_convention(np.array([[-0.5, 0.5, 0.5, -0.5]]))
+    assert np.array_equal(t, [[0.5, -0.5, -0.5, 0.5]])
+
+
+def test_eigvecs_pins_reject_planted_mistakes(oracle_mod):
+    """A transposed result and a column permutation not applied to lam both fail."""
+    A = inputs.goe(9, 33)
+    lam, vec = oracle_mod.eigvecs(A)
+
+    def residual(l, v):
+        return float(np.max(np.abs(A @ v.T - v.T * l[None, :])))
+    assert residual(lam, vec) < 1e-13
+    assert residual(lam, vec.T.copy()) > 1e-3                 # transposed output
+    perm = np.r_[1, 0, np.arange(2, 9)]
+    assert residual(lam, vec[perm]) > 1e-3                    # vectors permuted, lam not
