@@ -115,6 +115,28 @@ eeid_status eeid_components_host(eeid_ctx* ctx, const double* hA, int64_t lda, i
                                  int64_t ncols, double* h_out, double* h_lambda_opt,
                                  void* stream);
 
+/* Signed unit eigenvectors v_i for the eigen-indices i = h_rows[r] (r < nrows), every
+ * component j: d_vec[r*n + j] = v_ij (device, nrows x n doubles).  Eq. 1 fixes only
+ * |v_ij|; the signs come from applying it in a second basis (Sec. 2: the identity on
+ * other bases gives the direction).  For a reference component r of v_i, rotating
+ * coordinates r and j by 45 degrees and removing u = (e_r + e_j)/sqrt2 gives a minor
+ * whose Eq. 1 value is q_ij = (v_ir + v_ij)^2 / 2; then
+ *     v_ij = (q_ij - (|v_ir|^2 + |v_ij|^2) / 2) / |v_ir|   (v_ir > 0).
+ * References are chosen on the device by a greedy cover with |v_ir| >= max_j |v_ij| / 4,
+ * so the error of v_ij is about 2 delta / |v_ir| <= 8 sqrt(n) delta, delta being the
+ * error of |v_ij|^2.  Each reference costs one rotated minor per component (n - 1
+ * reductions): a few eigenvectors often share one reference, a whole eigenbasis of a
+ * random matrix needs about ten.
+ * Sign convention: the component of largest |v_ij|^2 (the first on exact ties) is
+ * positive.  Rows of eigenvalues that are exactly degenerate are NaN.
+ * h_rows: host, distinct indices in [0, n), NULL = all (nrows = n).  d_lambda_opt:
+ * optional device buffer of n doubles for the eigenvalues of A.  The call runs on
+ * `stream` and synchronises it once, midway, to read the chosen references back; it
+ * returns with the last phase enqueued.  Deferred warnings as for eeid_components. */
+eeid_status eeid_eigenvectors(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n,
+                              const int64_t* h_rows, int64_t nrows, double* d_vec,
+                              double* d_lambda_opt, void* stream);
+
 /* One problem of a batch: the arguments of eeid_components.  h_rows / h_cols NULL
  * mean "all" (nrows / ncols = n). */
 typedef struct {
@@ -156,6 +178,10 @@ eeid_status eeid_set_overlap(eeid_ctx* ctx, int enable);
 
 /* Number of kernel launches the context has enqueued so far (for accounting). */
 int64_t eeid_launch_count(const eeid_ctx* ctx);
+
+/* Number of reference components the context's last eeid_eigenvectors call chose
+ * (each costs n - 1 rotated-minor reductions); 0 before any such call. */
+int64_t eeid_vector_refs(const eeid_ctx* ctx);
 
 /* Tuning of the Householder kernel (K-a): matrices of size m in [m_lo, m_hi] are
  * reduced by the variant `path` (0 = working matrix resident in shared memory,
@@ -282,6 +308,19 @@ eeid_status eeid_server_cancel(eeid_server* srv, uint64_t ticket);
 /* Counters of the serving loop. */
 eeid_status eeid_server_info(eeid_server* srv, eeid_server_info_t* info);
 
+/* Bits of a device-side status word (OR-ed by the kernels while they run).  The context
+ * calls report them through eeid_sync; eeid_eigvals_noalloc writes them to a word the
+ * caller supplies. */
+enum {
+  EEID_DEV_DEGENERATE = 1u,       /* two eigenvalues of A exactly equal (Eq. 1 is 0/0) */
+  EEID_DEV_SMALL_GAP = 2u,        /* minimum relative gap below 1e-4 */
+  EEID_DEV_BRACKET_FALLBACK = 4u, /* a bisection bracket failed its check and restarted from
+                                     the Gershgorin bracket (information only: the result
+                                     is still correct) */
+  EEID_DEV_BAD_TASK = 8u          /* a kernel met a matrix beyond its size limit and skipped
+                                     it: the output for that matrix was not written */
+};
+
 /* Eigenvalues of A, like eeid_eigvals, for callers that cannot allocate device
  * memory: for example code embedded in an application whose own memory pool owns
  * the whole device, or code on a latency-critical path where the implicit device
@@ -294,16 +333,25 @@ eeid_status eeid_server_info(eeid_server* srv, eeid_server_info_t* info);
  * n > 512 returns EEID_ERR_INVALID with a message in eeid_last_error().  Every
  * call on a device uses the same array, so calls that overlap on the GPU (for
  * example on two streams without ordering) race and must be avoided; calls on one
- * stream are ordered and safe.  The first call on each device looks the array's
- * address up (with that device current) and caches it; make that first call before
- * any stream capture.
+ * stream are ordered and safe.
+ *
+ * First call on each device: it looks the array's address up (with that device
+ * current) and caches it, and it loads the library's kernels and raises their
+ * shared-memory limits.  Loading a module and changing a kernel attribute may wait
+ * for work already queued on the device, so make that first call before any stream
+ * capture and outside latency-critical sections; later calls do none of this.
  *
  * dA: device, row-major, lower triangle read, lda >= n.  d_lambda: device, n
- * doubles, ascending.  Asynchronous on `stream` (the calling thread's current
- * device); n == 0 is a no-op.  Results agree with eeid_eigvals within the library's
- * eigenvalue tolerance (1e-12 * ||A||_2). */
+ * doubles, ascending.  d_status_opt: optional device word (NULL = not reported).
+ * The call sets it to 0 on `stream` before its kernels run; they OR in EEID_DEV_*
+ * bits, which the caller reads once the stream has reached the end of the call.
+ * EEID_DEV_BAD_TASK there means d_lambda was not written.  Without the word,
+ * device-side conditions go unreported.  Asynchronous on `stream` (the calling
+ * thread's current device); n == 0 is a no-op (d_status_opt untouched).  Results
+ * agree with eeid_eigvals within the library's eigenvalue tolerance
+ * (1e-12 * ||A||_2). */
 eeid_status eeid_eigvals_noalloc(const double* dA, int64_t lda, int64_t n, double* d_lambda,
-                                 void* stream);
+                                 unsigned* d_status_opt, void* stream);
 
 #ifdef __cplusplus
 }

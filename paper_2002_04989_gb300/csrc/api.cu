@@ -16,6 +16,13 @@
 
 namespace eeid {
 int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m);
+cudaError_t preload_vectors();
+size_t pick_refs_smem_bytes(int nrows, int n);
+cudaError_t launch_pick_refs(const double* g, int nrows, int n, int* refs, int* row_ref,
+                             int* nref, cudaStream_t s);
+cudaError_t launch_signed(const void* rows, int nrows, int n, cudaStream_t s);
+size_t signed_row_bytes();
+void fill_signed_row(void* dst, const double* g, const double* q, double* out, int ref);
 }
 
 using namespace eeid;
@@ -100,6 +107,15 @@ struct eeid_ctx {
   bool timing = false;
   cudaEvent_t ev[EEID_NUM_PHASES][2] = {};
   bool ran[EEID_NUM_PHASES] = {};
+  // eeid_eigenvectors: its device buffers (magnitudes, rotated components, references)
+  // and a pinned buffer for the references read back and the rows uploaded.
+  char* vbuf = nullptr;
+  size_t vbuf_cap = 0;
+  char* h_vec = nullptr;
+  size_t h_vec_cap = 0;
+  cudaEvent_t vec_ev = nullptr;
+  bool vec_used = false;
+  int64_t vec_refs = 0;
 };
 
 namespace {
@@ -144,6 +160,12 @@ struct Problem {
   double* mu_user;        // minor-eigvals mode output (ncols x (n-1))
   bool all_rows = false;  // rows / cols given as NULL ("all")
   bool all_cols = false;
+  // Sign recovery: every minor of this problem is the rotated minor of (rot, j)
+  // (see TridiagTask); rot is never among the cols.
+  int rot = -1;
+  // Eigenvalues of A computed earlier on the same stream: A is not reduced or bisected
+  // again, and these seed the minors' brackets and the denominators.
+  const double* lam_in = nullptr;
 };
 
 enum Mode { MODE_EIGVALS, MODE_MINORS, MODE_COMPONENTS };
@@ -293,6 +315,8 @@ std::string batch_key(const std::vector<Problem>& probs, bool timing, int rules_
     put(&P.n, sizeof P.n);
     put(&P.out, sizeof P.out);
     put(&P.lam_user, sizeof P.lam_user);
+    put(&P.rot, sizeof P.rot);
+    put(&P.lam_in, sizeof P.lam_in);
     const int nr = (int)P.rows.size(), nc = (int)P.cols.size();
     const char flags = (char)((P.all_rows ? 1 : 0) | (P.all_cols ? 2 : 0));
     put(&flags, 1);
@@ -319,7 +343,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   for (int p = 0; p < (int)probs.size(); ++p) {
     const Problem& P = probs[p];
     if (P.n < 1) continue;
-    tri.push_back({p, -1, P.n});
+    if (!P.lam_in) tri.push_back({p, -1, P.n});
     if (mode != MODE_EIGVALS && P.n >= 2)
       for (int c = 0; c < (int)P.cols.size(); ++c) tri.push_back({p, c, P.n - 1});
   }
@@ -339,7 +363,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     const Problem& P = probs[p];
     max_n = std::max(max_n, P.n);
     if (P.n < 1) continue;
-    lam_off[p] = P.lam_user ? SIZE_MAX : dat.take(sizeof(double) * P.n);
+    lam_off[p] = (P.lam_user || P.lam_in) ? SIZE_MAX : dat.take(sizeof(double) * P.n);
     if (mode != MODE_EIGVALS && P.n >= 2)
       mu_off[p] = (mode == MODE_MINORS) ? SIZE_MAX
                                         : dat.take(sizeof(double) * P.cols.size() * (P.n - 1));
@@ -509,7 +533,10 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     img = ctx->h_stage;
   }
   memset(img, 0, meta_bytes);
-  auto lam_ptr = [&](int p) { return probs[p].lam_user ? probs[p].lam_user : D(lam_off[p]); };
+  auto lam_ptr = [&](int p) {
+    return probs[p].lam_in ? const_cast<double*>(probs[p].lam_in)
+                           : probs[p].lam_user ? probs[p].lam_user : D(lam_off[p]);
+  };
   auto mu_ptr = [&](int p) {
     return mode == MODE_MINORS ? probs[p].mu_user : D(mu_off[p]);
   };
@@ -519,7 +546,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
       const TriRef& r = tri[g.idx[q]];
       const Problem& P = probs[r.prob];
       tt[q] = {P.dA, P.lda, P.n, r.col < 0 ? -1 : P.cols[r.col], D(d_off[g.idx[q]]),
-               D(e_off[g.idx[q]])};
+               D(e_off[g.idx[q]]), r.col < 0 ? -1 : P.rot, 0};
     }
   }
   {
@@ -718,6 +745,7 @@ eeid_status eeid_ctx_create(int device, size_t hbm_budget_bytes, eeid_ctx** out)
   if (e == cudaSuccess) e = preload_tridiag();
   if (e == cudaSuccess) e = preload_bisect();
   if (e == cudaSuccess) e = preload_identity();
+  if (e == cudaSuccess) e = preload_vectors();
   if (e != cudaSuccess) {
     eeid_ctx_destroy(c);
     return cuda_fail(e, "context setup");
@@ -739,6 +767,9 @@ void eeid_ctx_destroy(eeid_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+  if (ctx->vbuf) cudaFree(ctx->vbuf);
+  if (ctx->h_vec) cudaFreeHost(ctx->h_vec);
+  if (ctx->vec_ev) cudaEventDestroy(ctx->vec_ev);
   for (int p = 0; p < EEID_NUM_PHASES; ++p)
     for (int w = 0; w < 2; ++w)
       if (ctx->ev[p][w]) cudaEventDestroy(ctx->ev[p][w]);
@@ -746,6 +777,8 @@ void eeid_ctx_destroy(eeid_ctx* ctx) {
 }
 
 int64_t eeid_launch_count(const eeid_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int64_t eeid_vector_refs(const eeid_ctx* ctx) { return ctx ? ctx->vec_refs : 0; }
 
 eeid_status eeid_tune_tridiag(eeid_ctx* ctx, int m_lo, int m_hi, int path, int warps) {
   eeid_status st = check_ctx(ctx);
@@ -1147,6 +1180,120 @@ eeid_status eeid_components_host(eeid_ctx* ctx, const double* hA, int64_t lda, i
     return st;
   }
   return eeid_sync(ctx, stream);
+}
+
+
+eeid_status eeid_eigenvectors(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n,
+                              const int64_t* h_rows, int64_t nrows, double* d_vec,
+                              double* d_lambda_opt, void* stream) {
+  eeid_status st = check_ctx(ctx);
+  if (st == EEID_OK) st = check_matrix(dA, lda, n);
+  if (st != EEID_OK) return st;
+  std::vector<int> rows;
+  st = parse_indices(h_rows, nrows, n, "rows", rows);
+  if (st != EEID_OK) return st;
+  if (n == 0 || nrows == 0) return EEID_OK;
+  if (!d_vec) return fail(EEID_ERR_INVALID, "d_vec is NULL");
+  EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = (int)n, NR = (int)nrows;
+  // ---- buffers: |v|^2 rows, rotated components, eigenvalues, references, row table
+  Arena ar;
+  const size_t g_off = ar.take(sizeof(double) * (size_t)NR * N);
+  const size_t q_off = ar.take(sizeof(double) * (size_t)NR * std::max(N - 1, 1));
+  const size_t l_off = ar.take(sizeof(double) * N);
+  const size_t r_off = ar.take(sizeof(int) * (1 + 2 * (size_t)NR));
+  const size_t s_off = ar.take(signed_row_bytes() * NR);
+  if (ar.off > ctx->budget)
+    return fail(EEID_ERR_NOMEM, "eigenvector buffers of %zu bytes exceed the HBM budget", ar.off);
+  if (ar.off > ctx->vbuf_cap) {
+    if (ctx->vbuf) {
+      cudaError_t e = cudaFree(ctx->vbuf);   // synchronises the device
+      ctx->vbuf = nullptr;
+      ctx->vbuf_cap = 0;
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFree(eigenvector buffers)");
+    }
+    cudaError_t e = cudaMalloc((void**)&ctx->vbuf, ar.off);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(EEID_ERR_NOMEM, "cudaMalloc(%zu) for the eigenvector buffers failed", ar.off);
+    }
+    ctx->vbuf_cap = ar.off;
+  }
+  const size_t h_bytes = std::max(sizeof(int) * (1 + 2 * (size_t)NR), signed_row_bytes() * NR);
+  if (ctx->vec_used) EEID_CK(cudaEventSynchronize(ctx->vec_ev), "cudaEventSynchronize(vectors)");
+  if (!ctx->vec_ev) EEID_CK(cudaEventCreateWithFlags(&ctx->vec_ev, cudaEventDisableTiming), "event");
+  if (h_bytes > ctx->h_vec_cap) {
+    if (ctx->h_vec) cudaFreeHost(ctx->h_vec);
+    ctx->h_vec = nullptr;
+    ctx->h_vec_cap = 0;
+    EEID_CK(cudaMallocHost((void**)&ctx->h_vec, h_bytes), "cudaMallocHost(vectors)");
+    ctx->h_vec_cap = h_bytes;
+  }
+  char* vb = ctx->vbuf;
+  double* G = (double*)(vb + g_off);
+  double* Qg = (double*)(vb + q_off);
+  double* lam = d_lambda_opt ? d_lambda_opt : (double*)(vb + l_off);
+  int* ri = (int*)(vb + r_off);   // [nref | refs[NR] | row_ref[NR]]
+
+  // ---- phase 1: |v_ij|^2 for the requested rows, all components j (Eq. 1)
+  std::vector<Problem> p1(1);
+  p1[0].dA = dA; p1[0].lda = lda; p1[0].n = N; p1[0].rows = rows;
+  p1[0].cols.resize(N);
+  for (int j = 0; j < N; ++j) p1[0].cols[j] = j;
+  p1[0].all_rows = (h_rows == nullptr);
+  p1[0].all_cols = true;
+  p1[0].out = G;
+  p1[0].lam_user = lam;
+  st = run(ctx, p1, MODE_COMPONENTS, s);
+  if (st != EEID_OK) return st;
+  // ---- phase 2: references (greedy cover on the device), read back to plan phase 3
+  EEID_CK(launch_pick_refs(G, NR, N, ri + 1, ri + 1 + NR, ri, s), "pick_refs launch");
+  ctx->launches++;
+  int* h_ri = (int*)ctx->h_vec;
+  EEID_CK(cudaMemcpyAsync(h_ri, ri, sizeof(int) * (1 + 2 * (size_t)NR), cudaMemcpyDeviceToHost, s),
+          "cudaMemcpyAsync(references)");
+  EEID_CK(cudaStreamSynchronize(s), "cudaStreamSynchronize(references)");
+  const int R = h_ri[0];
+  if (R < 0 || R > NR) return fail(EEID_ERR_CUDA, "reference selection returned %d", R);
+  std::vector<int> refs(h_ri + 1, h_ri + 1 + R), row_ref(h_ri + 1 + NR, h_ri + 1 + 2 * NR);
+  ctx->vec_refs = R;
+  // ---- phase 3: one problem per reference r: the rotated minors (r, j), j != r, for
+  // the rows that chose r
+  std::vector<Problem> p3(R);
+  std::vector<size_t> q_base(R, 0);
+  std::vector<int> pos(NR, -1);
+  size_t qoff = 0;
+  for (int q = 0; q < R; ++q) {
+    Problem& P = p3[q];
+    for (int r = 0; r < NR; ++r)
+      if (row_ref[r] == q) { pos[r] = (int)P.rows.size(); P.rows.push_back(rows[r]); }
+    for (int j = 0; j < N; ++j)
+      if (j != refs[q]) P.cols.push_back(j);
+    P.dA = dA; P.lda = lda; P.n = N; P.rot = refs[q]; P.lam_in = lam;
+    P.out = Qg + qoff;
+    q_base[q] = qoff;
+    qoff += P.rows.size() * (size_t)(N - 1);
+  }
+  if (N >= 2 && R > 0) {
+    st = run(ctx, p3, MODE_COMPONENTS, s);
+    if (st != EEID_OK) return st;
+  }
+  // ---- phase 4: assemble the signed vectors and apply the sign convention
+  char* h_rows_img = ctx->h_vec;
+  for (int r = 0; r < NR; ++r) {
+    const int q = row_ref[r];
+    const double* qrow = q >= 0 ? Qg + q_base[q] + (size_t)pos[r] * (N - 1) : nullptr;
+    fill_signed_row(h_rows_img + signed_row_bytes() * r, G + (size_t)r * N, qrow,
+                    d_vec + (size_t)r * N, q >= 0 ? refs[q] : -1);
+  }
+  EEID_CK(cudaMemcpyAsync(vb + s_off, h_rows_img, signed_row_bytes() * NR, cudaMemcpyHostToDevice, s),
+          "cudaMemcpyAsync(signed rows)");
+  EEID_CK(cudaEventRecord(ctx->vec_ev, s), "cudaEventRecord(vectors)");
+  ctx->vec_used = true;
+  EEID_CK(launch_signed(vb + s_off, NR, N, s), "signed launch");
+  ctx->launches++;
+  return EEID_OK;
 }
 
 }  // extern "C"

@@ -43,6 +43,12 @@ enum : unsigned {
 // One matrix to reduce to symmetric tridiagonal form: the parent A (n x n,
 // row-major, lower triangle read) with row/column `skip` removed (skip < 0: A
 // itself).  Outputs d[m] and e[m-1], m = n - (skip >= 0).
+//
+// rot >= 0 (with skip >= 0, rot != skip) selects the rotated minor used for signs:
+// coordinates rot and skip are first rotated by 45 degrees, u = (e_rot + e_skip)/sqrt2
+// and w = (e_rot - e_skip)/sqrt2, and u is removed.  The minor keeps w in the place of
+// rot: its row there is (a_rot,k - a_skip,k)/sqrt2 and its diagonal entry
+// (a_rot,rot + a_skip,skip)/2 - a_rot,skip.  Eq. 1 on it gives (v_i,rot + v_i,skip)^2 / 2.
 struct TridiagTask {
   const double* A;
   int64_t lda;
@@ -50,6 +56,8 @@ struct TridiagTask {
   int skip;
   double* d;
   double* e;
+  int rot = -1;
+  int pad_ = 0;
 };
 
 // Largest m the shared-memory-resident path accepts, per CTA warp count.

@@ -43,19 +43,23 @@ constexpr size_t kOffStatus = 256;   // unsigned status word
 static_assert(sizeof(TridiagTask) <= 64, "descriptor layout");
 static_assert(sizeof(BisectTask) <= 64, "descriptor layout");
 static_assert(kOffItems + 4 * sizeof(BisectItem) <= kOffStatus, "descriptor layout");
+static_assert(ST_DEGENERATE == EEID_DEV_DEGENERATE && ST_SMALL_GAP == EEID_DEV_SMALL_GAP &&
+                  ST_BRACKET_FALLBACK == EEID_DEV_BRACKET_FALLBACK && ST_BAD_TASK == EEID_DEV_BAD_TASK,
+              "device status bits of the header");
 
 // The scratch: 2.2 MB held by every GPU that loads the library, for the life of
 // the process.  Every call uses it; calls that overlap on the GPU race.
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-// Writes the descriptors for one call and clears what must start at zero.
-__global__ void k_noalloc_setup(TridiagTask t, BisectTask b, int nitems) {
+// Writes the descriptors for one call and clears what must start at zero: the work
+// counter and the status word of this call (the caller's word, or the scratch's own).
+__global__ void k_noalloc_setup(TridiagTask t, BisectTask b, int nitems, unsigned* status) {
   char* meta = (char*)(g_noalloc_scratch + kSlotDoubles + kDEDoubles);
   if (threadIdx.x == 0) {
     *(TridiagTask*)(meta + kOffTask) = t;
     *(int*)(meta + kOffCounter) = 0;
     *(BisectTask*)(meta + kOffBisect) = b;
-    *(unsigned*)(meta + kOffStatus) = 0u;
+    *status = 0u;
   }
   if ((int)threadIdx.x < nitems) {
     BisectItem it;
@@ -72,7 +76,8 @@ eeid_status na_fail(eeid_status s, const std::string& msg) {
 }
 
 // Device address of the scratch array, looked up once per device (with that
-// device current) under a lock.
+// device current) under a lock.  The same first call loads the two kernels and raises
+// their shared-memory limits, so that later calls change no kernel attribute.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_ptr[kMaxDevices] = {};
@@ -88,6 +93,10 @@ eeid_status scratch_for_device(int dev, double** out) {
     if (e != cudaSuccess || !p)
       return na_fail(EEID_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") +
                                         cudaGetErrorString(e));
+    e = preload_tridiag();
+    if (e == cudaSuccess) e = preload_bisect();
+    if (e != cudaSuccess)
+      return na_fail(EEID_ERR_CUDA, std::string("kernel set-up failed: ") + cudaGetErrorString(e));
     g_ptr[dev] = (double*)p;
   }
   *out = g_ptr[dev];
@@ -99,7 +108,7 @@ eeid_status scratch_for_device(int dev, double** out) {
 extern "C" {
 
 eeid_status eeid_eigvals_noalloc(const double* dA, int64_t lda, int64_t n, double* d_lambda,
-                                 void* stream) {
+                                 unsigned* d_status_opt, void* stream) {
   if (n < 0) return na_fail(EEID_ERR_INVALID, "n < 0");
   if (n == 0) return EEID_OK;
   if (n > kNoAllocMaxN)
@@ -117,12 +126,14 @@ eeid_status eeid_eigvals_noalloc(const double* dA, int64_t lda, int64_t n, doubl
   double* d = base + kSlotDoubles;
   double* ev = d + kNoAllocMaxN;
   char* meta = (char*)(base + kSlotDoubles + kDEDoubles);
+  unsigned* status = d_status_opt ? d_status_opt : (unsigned*)(meta + kOffStatus);
 
   TridiagTask t;
   t.A = dA;
   t.lda = lda;
   t.n = (int)n;
   t.skip = -1;
+  t.rot = -1;
   t.d = d;
   t.e = ev;
   BisectTask b;
@@ -132,7 +143,7 @@ eeid_status eeid_eigvals_noalloc(const double* dA, int64_t lda, int64_t n, doubl
   b.parent = nullptr;
   b.eig = d_lambda;
   const int nitems = (int)((n + kBisectThreads - 1) / kBisectThreads);
-  k_noalloc_setup<<<1, 32, 0, s>>>(t, b, nitems);
+  k_noalloc_setup<<<1, 32, 0, s>>>(t, b, nitems, status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(EEID_ERR_CUDA, cudaGetErrorString(e));
 
@@ -143,11 +154,11 @@ eeid_status eeid_eigvals_noalloc(const double* dA, int64_t lda, int64_t n, doubl
   L.work = base;
   L.work_stride = (int64_t)kSlotDoubles;
   L.max_m = (int)n;
-  L.status = (unsigned*)(meta + kOffStatus);
+  L.status = status;
   e = launch_tridiag(false, kNoAllocWarps, 1, L, s);
   if (e != cudaSuccess) return na_fail(EEID_ERR_CUDA, cudaGetErrorString(e));
   e = launch_bisect((const BisectTask*)(meta + kOffBisect), (const BisectItem*)(meta + kOffItems),
-                    nitems, (int)n, (unsigned*)(meta + kOffStatus), s);
+                    nitems, (int)n, status, s);
   if (e != cudaSuccess) return na_fail(EEID_ERR_CUDA, cudaGetErrorString(e));
   return EEID_OK;
 }

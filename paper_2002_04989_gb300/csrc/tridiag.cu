@@ -302,12 +302,40 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
     }
 
     // a1: the minor view -- copy the lower triangle of A without row/col `skip`.
-    for (int r = warp; r < m; r += W) {
-      const int i = (skip >= 0 && r >= skip) ? r + 1 : r;
-      const double* Arow = task.A + (size_t)i * task.lda;
-      for (int c = lane; c <= r; c += 32) {
-        const int j = (skip >= 0 && c >= skip) ? c + 1 : c;
-        S[(size_t)r * ld + c] = Arow[j];
+    if (task.rot < 0) {
+      for (int r = warp; r < m; r += W) {
+        const int i = (skip >= 0 && r >= skip) ? r + 1 : r;
+        const double* Arow = task.A + (size_t)i * task.lda;
+        for (int c = lane; c <= r; c += 32) {
+          const int j = (skip >= 0 && c >= skip) ? c + 1 : c;
+          S[(size_t)r * ld + c] = Arow[j];
+        }
+      }
+    } else {
+      // the rotated minor (see TridiagTask): w = (e_rot - e_skip)/sqrt2 kept at the
+      // position of rot, every other row and column as in the plain minor
+      const int rot = task.rot;
+      const int rp = rot > skip ? rot - 1 : rot;
+      const double* A = task.A;
+      const int64_t lda = task.lda;
+      auto a_of = [A, lda](int i, int j) {
+        return i >= j ? A[(size_t)i * lda + j] : A[(size_t)j * lda + i];
+      };
+      for (int r = warp; r < m; r += W) {
+        const int i = r >= skip ? r + 1 : r;
+        for (int c = lane; c <= r; c += 32) {
+          const int j = c >= skip ? c + 1 : c;
+          double x;
+          if (r == rp && c == rp)
+            x = 0.5 * (a_of(rot, rot) + a_of(skip, skip)) - a_of(rot, skip);
+          else if (r == rp)
+            x = (a_of(rot, j) - a_of(skip, j)) * 0.70710678118654752440;
+          else if (c == rp)
+            x = (a_of(i, rot) - a_of(i, skip)) * 0.70710678118654752440;
+          else
+            x = A[(size_t)i * lda + j];
+          S[(size_t)r * ld + c] = x;
+        }
       }
     }
     __syncthreads();

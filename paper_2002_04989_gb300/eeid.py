@@ -26,6 +26,11 @@ EEID_ERR_TIMEOUT = -4
 EEID_ERR_BUSY = -5
 EEID_ERR_NOT_FOUND = -6
 EEID_ERR_CANCELLED = -7
+# device-side status bits (EEID_DEV_* in include/eeid.h)
+EEID_DEV_DEGENERATE = 1
+EEID_DEV_SMALL_GAP = 2
+EEID_DEV_BRACKET_FALLBACK = 4
+EEID_DEV_BAD_TASK = 8
 
 _lock = threading.Lock()
 _lib = None
@@ -73,14 +78,16 @@ SIGNATURES = {
                         ctypes.c_int),
     "eeid_components_host": ([_vp, _vp, _i64, _i64, _i64p, _i64, _i64p, _i64, _vp, _vp, _vp],
                              ctypes.c_int),
+    "eeid_eigenvectors": ([_vp, _vp, _i64, _i64, _i64p, _i64, _vp, _vp, _vp], ctypes.c_int),
     "eeid_components_batched": ([_vp, ctypes.POINTER(EeidProblem), _i64, _vp], ctypes.c_int),
     "eeid_launch_count": ([_vp], ctypes.c_int64),
+    "eeid_vector_refs": ([_vp], ctypes.c_int64),
     "eeid_set_timing": ([_vp, ctypes.c_int], ctypes.c_int),
     "eeid_tune_tridiag": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "eeid_tune_reset": ([_vp], ctypes.c_int),
     "eeid_autotune": ([_vp, ctypes.c_int, ctypes.c_char_p], ctypes.c_int),
     "eeid_phase_times": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
-    "eeid_eigvals_noalloc": ([_vp, _i64, _i64, _vp, _vp], ctypes.c_int),
+    "eeid_eigvals_noalloc": ([_vp, _i64, _i64, _vp, _vp, _vp], ctypes.c_int),
     "eeid_set_graphs": ([_vp, ctypes.c_int], ctypes.c_int),
     "eeid_set_overlap": ([_vp, ctypes.c_int], ctypes.c_int),
     "eeid_server_create": ([ctypes.c_int, ctypes.POINTER(EeidServerOpts), ctypes.POINTER(_vp)],
@@ -157,16 +164,47 @@ def _mat(A):
     return A, int(A.stride(0)) if A.shape[0] > 0 else max(1, A.shape[0])
 
 
-def eeid_eigvals_noalloc(A, out=None, stream=None):
+def _out(t, numel, like, name, dtype=None):
+    """A caller-supplied output the kernels write `numel` elements into: it must be a
+    contiguous CUDA tensor of the right dtype, on the device of `like`, with room for
+    all of them (the library writes through the raw pointer)."""
+    import torch
+    dtype = torch.float64 if dtype is None else dtype
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype):
+        raise TypeError(f"{name} must be a {dtype} CUDA tensor")
+    if t.device != like.device:
+        raise ValueError(f"{name} is on {t.device}, the matrix on {like.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call writes {numel}")
+    return t
+
+
+def _hout(a, numel, name):
+    """A caller-supplied host output: a C-contiguous float64 numpy array with room for
+    `numel` elements (the library writes through the raw pointer)."""
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError(f"{name} must be a C-contiguous float64 numpy array")
+    if a.size < numel:
+        raise ValueError(f"{name} holds {a.size} elements, the call writes {numel}")
+    return a
+
+
+def eeid_eigvals_noalloc(A, out=None, status=None, stream=None):
     """Eigenvalues of A without any device allocation by the library (n <= 512);
     see eeid_eigvals_noalloc in include/eeid.h.  `out` may be a preallocated
-    float64 CUDA tensor of n elements."""
+    float64 CUDA tensor of n elements; `status`, an int32 CUDA tensor of one
+    element, receives the call's EEID_DEV_* bits once the stream reaches the end
+    of the call."""
     import torch
     A, lda = _mat(A)
     n = A.shape[0]
-    lam = out if out is not None else torch.empty(n, dtype=torch.float64, device=A.device)
+    lam = (_out(out, n, A, "out") if out is not None
+           else torch.empty(n, dtype=torch.float64, device=A.device))
+    sp = _vp(_out(status, 1, A, "status", torch.int32).data_ptr()) if status is not None else None
     with torch.cuda.device(A.device):
-        _check(load().eeid_eigvals_noalloc(_vp(A.data_ptr()), lda, n, _vp(lam.data_ptr()),
+        _check(load().eeid_eigvals_noalloc(_vp(A.data_ptr()), lda, n, _vp(lam.data_ptr()), sp,
                                            _stream(stream)), False)
     return lam
 
@@ -206,7 +244,8 @@ class Context:
         import torch
         A, lda = _mat(A)
         n = A.shape[0]
-        lam = out if out is not None else torch.empty(n, dtype=torch.float64, device=A.device)
+        lam = (_out(out, n, A, "out") if out is not None
+               else torch.empty(n, dtype=torch.float64, device=A.device))
         _check(self.lib.eeid_eigvals(self.handle, _vp(A.data_ptr()), lda, n, _vp(lam.data_ptr()),
                                      _stream(stream)))
         return lam
@@ -217,8 +256,8 @@ class Context:
         n = A.shape[0]
         cp, nc, keep = _idx(cols)
         nc = n if cp is None else nc
-        mu = out if out is not None else torch.empty((nc, max(n - 1, 0)), dtype=torch.float64,
-                                                     device=A.device)
+        mu = (_out(out, nc * max(n - 1, 0), A, "out") if out is not None
+              else torch.empty((nc, max(n - 1, 0)), dtype=torch.float64, device=A.device))
         _check(self.lib.eeid_minor_eigvals(self.handle, _vp(A.data_ptr()), lda, n, cp, nc,
                                            _vp(mu.data_ptr()), _stream(stream)))
         return mu
@@ -231,11 +270,31 @@ class Context:
         cp, nc, k2 = _idx(cols)
         nr = n if rp is None else nr
         nc = n if cp is None else nc
-        o = out if out is not None else torch.empty((nr, nc), dtype=torch.float64, device=A.device)
+        o = (_out(out, nr * nc, A, "out") if out is not None
+             else torch.empty((nr, nc), dtype=torch.float64, device=A.device))
+        if lam is not None:
+            _out(lam, n, A, "lam")
         _check(self.lib.eeid_components(self.handle, _vp(A.data_ptr()), lda, n, rp, nr, cp, nc,
                                         _vp(o.data_ptr()),
                                         _vp(lam.data_ptr()) if lam is not None else None,
                                         _stream(stream)))
+        return o
+
+    def eeid_eigenvectors(self, A, rows=None, out=None, lam=None, stream=None):
+        """Signed unit eigenvectors: out[r, j] = v_ij for i = rows[r] (all if None)."""
+        import torch
+        A, lda = _mat(A)
+        n = A.shape[0]
+        rp, nr, k1 = _idx(rows)
+        nr = n if rp is None else nr
+        o = (_out(out, nr * n, A, "out") if out is not None
+             else torch.empty((nr, n), dtype=torch.float64, device=A.device))
+        if lam is not None:
+            _out(lam, n, A, "lam")
+        _check(self.lib.eeid_eigenvectors(self.handle, _vp(A.data_ptr()), lda, n, rp, nr,
+                                          _vp(o.data_ptr()),
+                                          _vp(lam.data_ptr()) if lam is not None else None,
+                                          _stream(stream)))
         return o
 
     def eeid_components_host(self, A: np.ndarray, rows=None, cols=None, out=None, lam=None,
@@ -246,7 +305,9 @@ class Context:
         cp, nc, k2 = _idx(cols)
         nr = n if rp is None else nr
         nc = n if cp is None else nc
-        o = out if out is not None else np.empty((nr, nc))
+        o = _hout(out, nr * nc, "out") if out is not None else np.empty((nr, nc))
+        if lam is not None:
+            _hout(lam, n, "lam")
         st = self.lib.eeid_components_host(
             self.handle, A.ctypes.data_as(_vp), n, n, rp, nr, cp, nc, o.ctypes.data_as(_vp),
             lam.ctypes.data_as(_vp) if lam is not None else None, _stream(stream))
@@ -270,9 +331,9 @@ class Context:
             arr[p].nrows = n if rp is None else nr
             arr[p].h_cols = cp
             arr[p].ncols = n if cp is None else nc
-            arr[p].d_out = d["out"].data_ptr()
+            arr[p].d_out = _out(d["out"], arr[p].nrows * arr[p].ncols, A, "out").data_ptr()
             lam = d.get("lam")
-            arr[p].d_lambda = lam.data_ptr() if lam is not None else None
+            arr[p].d_lambda = _out(lam, n, A, "lam").data_ptr() if lam is not None else None
         return _check(self.lib.eeid_components_batched(self.handle, arr, len(problems),
                                                        _stream(stream)))
 
@@ -287,6 +348,9 @@ class Context:
 
     def eeid_launch_count(self) -> int:
         return self.launch_count()
+
+    def eeid_vector_refs(self) -> int:
+        return int(self.lib.eeid_vector_refs(self.handle))
 
     def eeid_tune_tridiag(self, m_lo: int, m_hi: int, path: int, warps: int) -> int:
         return _check(self.lib.eeid_tune_tridiag(self.handle, m_lo, m_hi, path, warps), False)

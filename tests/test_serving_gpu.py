@@ -59,6 +59,33 @@ def test_results_same_alone_and_in_the_mix(torch_cuda):
         assert np.array_equal(out, o_ref) and np.array_equal(lam, l_ref)
 
 
+def test_served_results_against_oracle_and_closed_form(torch_cuda, oracle_mod):
+    """Served results against references that do not come from the GPU: planted
+    requests (n from 40 to 1300, so the 16-warp reductions and round-sized launches
+    of n > 1024 are covered) against the closed form Q o Q, GOE requests against the
+    long-double oracle.  Requests go in together, so they share batches and overlap."""
+    planted = [inputs.planted(n, 900 + n, -1.0, 1.0, 1e-4) for n in (40, 200, 520, 1100, 1300)]
+    goes = [inputs.goe(n, 950 + n) for n in (24, 61, 90)]
+    col_sets = [None, np.array([0, 7, 39]), None, np.array([3, 500, 1099]), np.arange(0, 1300, 97)]
+    with eeid.Server(0, max_batch=8, max_inflight=2) as srv:
+        tp = [srv.eeid_server_submit(p.A, cols=c) for p, c in zip(planted, col_sets)]
+        tg = [srv.eeid_server_submit(A) for A in goes]
+        res_p = [srv.eeid_server_wait(t) for t in tp]
+        res_g = [srv.eeid_server_wait(t) for t in tg]
+    for p, cols, (out, lam, st) in zip(planted, col_sets, res_p):
+        n = p.A.shape[0]
+        ref = (p.Q * p.Q).T if cols is None else (p.Q * p.Q).T[:, cols]
+        err = float(np.max(np.abs(out - ref)))
+        print(f"served planted n={n}: max|d vsq| = {err:.2e}")
+        assert err <= 1e-10, (n, err)
+        assert np.max(np.abs(lam - p.lam)) <= 1e-12
+    for A, (out, lam, st) in zip(goes, res_g):
+        ref, lam_ref, _ = oracle_mod.components(A, method=0, want_eigs=True)
+        bar = 1e-10 if inputs.min_relative_gap(lam_ref) >= 1e-4 else 1e-6
+        assert np.max(np.abs(out - ref)) <= bar, A.shape[0]
+        assert np.max(np.abs(lam - lam_ref)) <= 1e-12 * max(abs(lam_ref[0]), abs(lam_ref[-1]))
+
+
 def test_arrivals_overlap_a_running_batch(torch_cuda):
     """Small requests that arrive while a large batch runs start on the second slot
     and finish before it (continuous batching, not a FIFO queue)."""

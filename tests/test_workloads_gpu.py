@@ -76,8 +76,8 @@ def test_batch4096_one_batched_call(torch_cuda, ctx, oracle_mod):
             assert g["col_sum"] < 1e-9 and g["row_sum"] < 1e-9
         assert s["trace"] <= 1e-12 * norm * A.shape[0] and s["sorted"] == 0
     print(f"batch4096: worst row/col-sum deviation (gap clause met) = {worst:.3e}")
-    # sampled matrices (n <= 128, so the long-double oracle stays within seconds) against
-    # the oracle: n <= 64 in full, larger ones on sampled rows and columns
+    # sampled matrices against the long-double oracle: n <= 64 in full, larger ones on
+    # sampled rows and columns
     rng = np.random.default_rng(0)
     small = [i for i, A in enumerate(mats) if A.shape[0] <= 128]   # oracle cost bound
     for idx in rng.choice(small, 10, replace=False):
@@ -94,3 +94,35 @@ def test_batch4096_one_batched_call(torch_cuda, ctx, oracle_mod):
             got = out[np.ix_(rows, cols)]
         bar = TOL_VSQ if inputs.min_relative_gap(lam_ref) >= 1e-4 else 1e-6
         assert np.max(np.abs(got - ref)) <= bar, (idx, n)
+    # the sizes that carry most of the work (n in (128, 256], reduced by the autotuned
+    # global-slot variants): one GOE and one Wishart matrix on sampled rows and
+    # columns against the oracle, and every Toeplitz matrix of that range in full
+    # against its closed form (2/(n+1)) sin^2(i j pi/(n+1)), eigenvalues 2 cos(k pi/(n+1))
+    big = [i for i, A in enumerate(mats) if 192 < A.shape[0] <= 256]
+    for kind in ("goe", "wishart"):
+        idx = next(i for i in big if inputs.BATCH_KINDS[i % 3] == kind)
+        A = mats[idx]
+        n = A.shape[0]
+        rows = np.unique(np.r_[0, n // 2, n - 1, rng.choice(n, 3, replace=False)])
+        cols = np.unique(np.r_[0, n - 1, rng.choice(n, 1, replace=False)])
+        ref, lam_ref, _ = oracle_mod.components(A, rows=rows, cols=cols, method=0, want_eigs=True)
+        got = probs[idx]["out"].cpu().numpy()[np.ix_(rows, cols)]
+        lam = probs[idx]["lam"].cpu().numpy()
+        bar = TOL_VSQ if inputs.min_relative_gap(lam_ref) >= 1e-4 else 1e-6
+        err = float(np.max(np.abs(got - ref)))
+        print(f"batch4096 item {idx} ({kind}, n={n}): max|d vsq| = {err:.2e} on {rows.size}x{cols.size}")
+        assert err <= bar, (idx, n, err)
+        assert np.max(np.abs(lam - lam_ref)) <= TOL_LAM_REL * max(abs(lam_ref[0]), abs(lam_ref[-1]))
+    tops = [i for i, A in enumerate(mats) if A.shape[0] > 128 and inputs.BATCH_KINDS[i % 3] == "toeplitz"]
+    worst = 0.0
+    for idx in tops:
+        n = mats[idx].shape[0]
+        k = np.arange(1, n + 1)
+        vsq_c = 2.0 / (n + 1) * np.sin(np.outer(k, k) * np.pi / (n + 1)) ** 2
+        lam_c = 2.0 * np.cos(k * np.pi / (n + 1))
+        order = np.argsort(lam_c)        # ascending relabelling of the sine vectors
+        got = probs[idx]["out"].cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(got - vsq_c[order]))))
+        assert np.max(np.abs(probs[idx]["lam"].cpu().numpy() - lam_c[order])) <= TOL_LAM_REL * 2.0
+    print(f"batch4096: {len(tops)} Toeplitz matrices with n > 128, max|d vsq| vs closed form = {worst:.2e}")
+    assert worst <= TOL_VSQ
