@@ -59,6 +59,9 @@ def _load():
                 "oracle_secular_minor_eigvals": [_i64, _dp, _dp, _ip, _i64, _dp],
                 "oracle_inverse_iteration": [_i64, _dp, _i64, ctypes.c_double, ctypes.c_int, _dp],
                 "oracle_real_mant_dig": [],
+                "oracle_components_herm": [_i64, _dp, _i64, _ip, _i64, _ip, _i64, ctypes.c_int,
+                                           _dp, _dp],
+                "oracle_minor_eigvals_herm": [_i64, _dp, _i64, _ip, _i64, _dp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -207,3 +210,35 @@ def inverse_iteration(A, shift, iters=3):
     _check(_load().oracle_inverse_iteration(n, _d(A), n, float(shift), int(iters), _d(x)),
            "oracle_inverse_iteration")
     return x
+
+
+def _herm(A):
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    assert A.ndim == 2 and A.shape[0] == A.shape[1]
+    return A, A.view(np.float64)
+
+
+def components_herm(A, rows=None, cols=None, method=0, want_eigs=False):
+    """|v_ij|^2 of a complex Hermitian A (lower triangle read) in long double, through
+    the real symmetric embedding [[Re, -Im], [Im, Re]]: method 0 = Jacobi eigenvalues
+    of A and every M_j, then Eq. 1; method 2 = the embedding's eigenvectors."""
+    A, Af = _herm(A)
+    n = A.shape[0]
+    r, nr = _idx(rows, n)
+    c, nc = _idx(cols, n)
+    out = np.empty((nr, nc))
+    lam = np.empty(n)
+    _check(_load().oracle_components_herm(n, _d(Af), n, _i(r), nr, _i(c), nc, method, _d(out),
+                                          _d(lam)), "oracle_components_herm")
+    return (out, lam) if want_eigs else out
+
+
+def minor_eigvals_herm(A, cols=None):
+    """mu[c, k]: ascending eigenvalues of the minors M_j of Hermitian A, j = cols[c]."""
+    A, Af = _herm(A)
+    n = A.shape[0]
+    c, nc = _idx(cols if cols is not None else np.arange(n), n)
+    mu = np.empty((nc, max(n - 1, 0)))
+    _check(_load().oracle_minor_eigvals_herm(n, _d(Af), n, _i(c), nc, _d(mu)),
+           "oracle_minor_eigvals_herm")
+    return mu

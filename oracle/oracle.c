@@ -40,6 +40,11 @@
  *                                     (Cramer's rule: ((mu I - A)^-1)_jj =
  *                                     det(mu I - M_j) / det(mu I - A); textbook, not
  *                                     the paper), one bisection per pole interval.
+ *   oracle_components_herm,           the same for a complex Hermitian A (Sec. 2 states
+ *   oracle_minor_eigvals_herm         Eq. 1 for Hermitian matrices), through the real
+ *                                     symmetric 2n x 2n embedding [[Re, -Im], [Im, Re]],
+ *                                     whose spectrum is A's with every eigenvalue doubled
+ *                                     (textbook); Jacobi as above on the embedding.
  *   oracle_inverse_iteration          brute-force eigenvector by shifted inverse
  *                                     iteration with Gaussian elimination (partial
  *                                     pivoting); for tiny n only.
@@ -462,6 +467,122 @@ int oracle_inverse_iteration(int64_t n, const double* A, int64_t lda, double shi
   for (int64_t i = 0; i < n; ++i) x[i] = (double)b[i];
   free(M); free(b); free(y); free(piv);
   return 0;
+}
+
+/* ---------------------------------------------------------------- Hermitian A */
+
+/* Real symmetric embedding of a complex Hermitian matrix H (Sec. 2 states Eq. 1 for
+ * Hermitian matrices).  H is row-major with interleaved (re, im) doubles, leading
+ * dimension lda in complex elements, lower triangle read (H_cr = conj(H_rc)); row and
+ * column `skip` are removed when skip >= 0.  With m = n or n - 1 the result is the
+ * 2m x 2m matrix E = [[Re H, -Im H], [Im H, Re H]] (full storage).  H v = lam v with
+ * v = a + i b is E (a; b) = lam (a; b), and E (-b; a) = lam (-b; a) as well, so every
+ * eigenvalue of H is a double eigenvalue of E.  Textbook, not the paper. */
+static void load_herm_embed(int64_t n, const double* H, int64_t lda, int64_t skip, real* E) {
+  int64_t m = (skip >= 0) ? n - 1 : n;
+  int64_t M = 2 * m;
+  for (int64_t r = 0; r < m; ++r) {
+    int64_t i = (skip >= 0 && r >= skip) ? r + 1 : r;
+    for (int64_t c = 0; c <= r; ++c) {
+      int64_t j = (skip >= 0 && c >= skip) ? c + 1 : c;
+      real re = (real)H[2 * (i * lda + j)];
+      real im = (r == c) ? 0 : (real)H[2 * (i * lda + j) + 1];  /* diagonal is real */
+      /* H_rc = re + i im, H_cr = re - i im */
+      E[r * M + c] = re;            E[c * M + r] = re;
+      E[(m + r) * M + (m + c)] = re; E[(m + c) * M + (m + r)] = re;
+      E[(m + r) * M + c] = im;      E[c * M + (m + r)] = im;      /* Im H_rc, and its transpose */
+      E[(m + c) * M + r] = -im;     E[r * M + (m + c)] = -im;     /* Im H_cr = -im */
+    }
+  }
+}
+
+/* Ascending eigenvalues of H (skip < 0) or of its minor without row/col skip, from the
+ * Jacobi eigenvalues of the embedding (each appears twice; the pair is averaged).  With
+ * vsq != NULL (skip < 0 only) also the squared moduli of the unit eigenvectors:
+ * vsq[i*n + j] = |v_ij|^2 = half the sum, over the two embedding eigenvectors of the
+ * pair, of x_j^2 + x_{n+j}^2 (the diagonal of the projector onto the pair's plane). */
+static int herm_eig_ld(int64_t n, const double* H, int64_t lda, int64_t skip, real* lam,
+                       real* vsq) {
+  int64_t m = (skip >= 0) ? n - 1 : n;
+  if (m <= 0) return 0;
+  int64_t M = 2 * m;
+  real* E = (real*)malloc(sizeof(real) * M * M);
+  real* V = vsq ? (real*)malloc(sizeof(real) * M * M) : NULL;
+  real* l = (real*)malloc(sizeof(real) * M);
+  if (!E || !l || (vsq && !V)) { free(E); free(V); free(l); return -2; }
+  load_herm_embed(n, H, lda, skip, E);
+  jacobi(M, E, V);
+  sorted_eig(M, E, V, l);
+  for (int64_t i = 0; i < m; ++i) {
+    lam[i] = (l[2 * i] + l[2 * i + 1]) / 2;
+    if (vsq)
+      for (int64_t j = 0; j < m; ++j) {
+        real s = 0;
+        for (int64_t t = 2 * i; t <= 2 * i + 1; ++t)
+          s += V[j * M + t] * V[j * M + t] + V[(m + j) * M + t] * V[(m + j) * M + t];
+        vsq[i * m + j] = s / 2;
+      }
+  }
+  free(E); free(V); free(l);
+  return 0;
+}
+
+/* Hermitian A -> |v_ij|^2 in long double (same conventions as oracle_components; A is
+ * interleaved complex with leading dimension lda in complex elements):
+ *   method 0: eigenvalues of A and of each minor M_j from the embedding, then Eq. 1;
+ *   method 2: |v_ij|^2 from the embedding's eigenvectors (plain definition). */
+int oracle_components_herm(int64_t n, const double* A, int64_t lda, const int64_t* rows,
+                           int64_t nrows, const int64_t* cols, int64_t ncols, int method,
+                           double* out, double* lam_out) {
+  if (n < 1 || !A || lda < n || nrows < 0 || ncols < 0 || (method != 0 && method != 2)) return -1;
+  if ((rows && check_indices(n, rows, nrows)) || (cols && check_indices(n, cols, ncols))) return -1;
+  if ((!rows && nrows != n) || (!cols && ncols != n)) return -1;
+  if (nrows > 0 && ncols > 0 && !out) return -1;
+  real* l = (real*)malloc(sizeof(real) * n);
+  real* vsq = method == 2 ? (real*)malloc(sizeof(real) * n * n) : NULL;
+  if (!l || (method == 2 && !vsq)) { free(l); free(vsq); return -2; }
+  int rc = herm_eig_ld(n, A, lda, -1, l, vsq);
+  if (lam_out) for (int64_t k = 0; k < n; ++k) lam_out[k] = (double)l[k];
+  int bad = 0;
+  if (method == 2) {
+    for (int64_t r = 0; r < nrows; ++r)
+      for (int64_t c = 0; c < ncols; ++c) {
+        int64_t i = rows ? rows[r] : r, j = cols ? cols[c] : c;
+        out[r * ncols + c] = (double)vsq[i * n + j];
+      }
+  } else {
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int64_t c = 0; c < ncols; ++c) {
+      int64_t j = cols ? cols[c] : c;
+      real* u = (real*)malloc(sizeof(real) * (n > 1 ? n - 1 : 1));
+      if (!u) { bad |= 1; continue; }
+      if (herm_eig_ld(n, A, lda, j, u, NULL)) bad |= 1;
+      for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows ? rows[r] : r;
+        out[r * ncols + c] = (double)identity_one(n, l, u, i, 0);
+      }
+      free(u);
+    }
+  }
+  free(l); free(vsq);
+  return (rc || bad) ? -2 : 0;
+}
+
+/* Ascending eigenvalues of the minors M_j of Hermitian A: mu[c*(n-1) + k]. */
+int oracle_minor_eigvals_herm(int64_t n, const double* A, int64_t lda, const int64_t* cols,
+                              int64_t ncols, double* mu) {
+  if (n < 1 || !A || lda < n || ncols < 0 || (ncols > 0 && (!cols || !mu))) return -1;
+  if (check_indices(n, cols, ncols)) return -1;
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+  for (int64_t c = 0; c < ncols; ++c) {
+    real* u = (real*)malloc(sizeof(real) * (n > 1 ? n - 1 : 1));
+    if (!u) { bad |= 1; continue; }
+    if (herm_eig_ld(n, A, lda, cols[c], u, NULL)) bad |= 1;
+    for (int64_t k = 0; k < n - 1; ++k) mu[c * (n - 1) + k] = (double)u[k];
+    free(u);
+  }
+  return bad ? -2 : 0;
 }
 
 /* Number of bits of precision of `real` on this host (64 on x86 x87, 113 on

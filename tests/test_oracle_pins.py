@@ -335,3 +335,87 @@ def test_eigvecs_pins_reject_planted_mistakes(oracle_mod):
     assert residual(lam, vec.T.copy()) > 1e-3                 # transposed output
     perm = np.r_[1, 0, np.arange(2, 9)]
     assert residual(lam, vec[perm]) > 1e-3                    # vectors permuted, lam not
+
+
+# ------------------------------------------------------------------ Hermitian A
+# Sec. 2 states Eq. 1 for Hermitian matrices.  The oracle handles a complex Hermitian A
+# through its real symmetric embedding; these pins do not use that construction.
+
+def herm_goe(n, seed):
+    g = np.random.default_rng(seed)
+    G = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    return (G + G.conj().T) / 2
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_herm_2x2_closed_form(oracle_mod, seed):
+    g = np.random.default_rng(400 + seed)
+    a, c = g.standard_normal(2)
+    b = complex(*g.standard_normal(2))
+    A = np.array([[a, np.conj(b)], [b, c]])       # lower triangle holds b
+    h = math.sqrt(((a - c) / 2) ** 2 + abs(b) ** 2)
+    lp, lm = (a + c) / 2 + h, (a + c) / 2 - h
+    # row 0 of (A - lam I) x = 0: (a - lam) x0 + conj(b) x1 = 0 -> x = (conj(b), lam - a)
+    p0 = abs(b) ** 2 / (abs(b) ** 2 + (lp - a) ** 2)   # |x0|^2 / |x|^2 for lam_+
+    expect = np.array([[1 - p0, p0], [p0, 1 - p0]])
+    for method in (0, 2):
+        out, lam = oracle_mod.components_herm(A, method=method, want_eigs=True)
+        assert np.allclose(lam, [lm, lp], rtol=0, atol=1e-15 * (abs(lp) + abs(lm) + 1))
+        assert np.max(np.abs(out - expect)) < 1e-14, method
+    mu = oracle_mod.minor_eigvals_herm(A)
+    assert mu[0, 0] == c and mu[1, 0] == a
+
+
+@pytest.mark.parametrize("n,theta", [(5, 0.7), (16, -2.1), (33, 1.0)])
+def test_herm_toeplitz_with_phase(oracle_mod, n, theta):
+    """Off-diagonals e^{i theta} (below) and e^{-i theta} (above): the diagonal phase
+    similarity D = diag(e^{i k theta}) makes it the real Toeplitz (0, 1), so the
+    eigenvalues are 2 cos(k pi/(n+1)) and |v_ij|^2 the squared sine vectors."""
+    A = np.zeros((n, n), dtype=complex)
+    idx = np.arange(n - 1)
+    A[idx + 1, idx] = np.exp(1j * theta)
+    A[idx, idx + 1] = np.exp(-1j * theta)
+    lam_c, vsq_c = toeplitz_closed(n, 0.0, 1.0)
+    for method in (0, 2):
+        out, lam = oracle_mod.components_herm(A, method=method, want_eigs=True)
+        assert np.max(np.abs(lam - lam_c)) < 1e-14
+        assert np.max(np.abs(out - vsq_c)) < 1e-13, method
+
+
+def test_herm_real_input_matches_real_oracle(oracle_mod):
+    A = inputs.goe(20, 5)
+    a = oracle_mod.components(A, method=0)
+    b = oracle_mod.components_herm(A.astype(complex), method=0)
+    assert np.max(np.abs(a - b)) < 1e-15
+
+
+@pytest.mark.parametrize("n", [7, 30])
+def test_herm_against_lapack_and_invariants(oracle_mod, n):
+    A = herm_goe(n, 500 + n)
+    w, V = np.linalg.eigh(A)
+    out, lam = oracle_mod.components_herm(A, method=0, want_eigs=True)
+    assert np.max(np.abs(lam - w)) < 1e-13
+    assert np.max(np.abs(out - (np.abs(V) ** 2).T)) < 1e-14 / np.min(np.diff(w))
+    g = grid_errors(A.real, lam, out)        # the diagonal of a Hermitian A is real
+    assert g["col_sum"] < 1e-13 and g["row_sum"] < 1e-13 and g["diag"] < 1e-13
+    mu = oracle_mod.minor_eigvals_herm(A)
+    lo = lam[:-1][None, :] - mu
+    hi = mu - lam[1:][None, :]
+    assert max(lo.max(), hi.max()) <= 1e-14                    # Cauchy interlacing
+    assert np.max(np.abs(mu.sum(axis=1) - (np.trace(A).real - np.diag(A).real))) < 1e-12
+
+
+def test_herm_planted_and_phase_invariance(oracle_mod):
+    g = np.random.default_rng(9)
+    n = 24
+    Q, _ = np.linalg.qr(g.standard_normal((n, n)) + 1j * g.standard_normal((n, n)))
+    lam = np.sort(g.uniform(-1, 1, n))
+    A = (Q * lam) @ Q.conj().T
+    A = np.tril(A) + np.tril(A, -1).conj().T
+    out = oracle_mod.components_herm(A, method=0)
+    assert np.max(np.abs(out - (np.abs(Q) ** 2).T)) < 1e-12
+    # a diagonal unitary similarity D A D^H multiplies each eigenvector's components by
+    # phases only, so it changes no |v_ij|^2
+    D = np.exp(1j * g.uniform(0, 2 * np.pi, n))
+    B = (D[:, None] * A) * D.conj()[None, :]
+    assert np.max(np.abs(oracle_mod.components_herm(B, method=0) - out)) < 1e-12
