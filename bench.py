@@ -49,7 +49,7 @@ TRIDIAG_FLOPS = 4.0 / 3.0 * (N ** 3 + N * (N - 1) ** 3)
 # is unchanged: sha256 of csrc/tridiag.cu up to the end of its anonymous namespace,
 # which holds every device function (host-side launch code below it may change).
 TRIDIAG_TRAFFIC = {"bytes_per_launch": 3.195e12,
-                   "device_code_sha256": "8a61f9f29da280519383f0779a873a3e679074280dc71923466e8503bd55a773"}
+                   "device_code_sha256": "7efbacc13defdbb2f3e2275249eb6126181d76c70b47a211e0a56621aba66f3e"}
 
 
 def device_code_sha(path: str) -> str:
@@ -295,6 +295,24 @@ def run_gpu(args, world, rank, local):
                "sample": (f"{c} columns j of the same matrix ({c * N} components, {dt:.1f} s): "
                           f"minor eigenvalues by secular-equation bisection from the planted "
                           f"(lam, Q), then Eq. 1, long double, OpenMP over columns")}
+    workloads = None
+    if world == 1 and not args.no_workloads:
+        # the other workloads, each timed after the headline's timed region, with its own
+        # events, clocks and roofline (goe64: 3+10 calls; batch4096: 3+2 batched steps and
+        # one plain pass; planted4096 and vectors1024: 1+1 steps; serving: one rate)
+        workloads = {}
+        ctx.eeid_tune_reset()
+        for name, st_, wu in (("goe64", 10, 3), ("batch4096", 2, 3), ("planted4096", 1, 1),
+                              ("vectors1024", 1, 1), ("herm1024", 1, 1), ("single4002", 3, 1)):
+            try:
+                workloads[name] = workload_record(name, ctx, dev, stream, st_, wu, local)
+            except Exception as ex:   # a failed sub-record must not hide the headline
+                workloads[name] = {"error": repr(ex)}
+            ctx.eeid_tune_reset()
+        try:
+            workloads["serving"] = serving_record(local, args.serving_requests, [2.0])
+        except Exception as ex:
+            workloads["serving"] = {"error": repr(ex)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
@@ -318,6 +336,7 @@ def run_gpu(args, world, rank, local):
         "phases_ms": phase_avg,
         "max_abs_err_vs_QoQ": err,
         "status": st,
+        "workloads": workloads,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -328,39 +347,58 @@ def tridiag_flops(sizes_and_cols) -> float:
     return sum(4.0 / 3.0 * (n ** 3 + nc * (n - 1) ** 3) for n, nc in sizes_and_cols)
 
 
-def run_other(args, world, rank, local):
-    """Lines for the other workloads: goe64 (one small matrix, all minors),
-    batch4096 (4096 matrices of uneven n in one batched call, against the plain
-    one-call-per-matrix loop) and planted4096 (n = 4096, 256 seeded columns)."""
+def alu_roofline(flops: float, ms: float, kernel: str) -> dict:
+    achieved = flops / (ms / 1e3) / 1e12 if ms and ms > 0 else None
+    peak = FP64_PEAK_GFLOPS / 1e3
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": None, "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"}
+
+
+def _timed(torch, stream, fn, steps):
+    """CUDA-event time of `steps` calls of fn on `stream` (ms, whole span)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def workload_record(name, ctx, dev, stream, steps, warmup, local=0):
+    """One other workload, timed after the headline: goe64 (one small matrix, all
+    minors), batch4096 (4096 matrices of uneven n in one batched call, against the plain
+    one-call-per-matrix loop), planted4096 (n = 4096, 256 seeded columns) and vectors1024
+    (signed eigenvectors of the planted n = 1024 matrix for 16 eigen-indices).  Returns a
+    dict with its own CUDA-event timing, roofline, clocks and status."""
     import numpy as np
     import torch
 
-    from paper_2002_04989_gb300 import eeid, inputs
-    torch.cuda.set_device(local)
-    dist = init_dist(world, "nccl")
-    dev = torch.device("cuda", local)
-    ctx = eeid.Context(local)
-    stream = torch.cuda.current_stream(dev)
+    from paper_2002_04989_gb300 import inputs
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    extra = {}
-    if args.workload == "batch4096":
+    rec = {}
+    plain_step = None
+    phase_timed = True
+    if name == "batch4096":
         # per-size kernel variants picked by the autotuner (cached per device model)
         tune_path = os.path.join(ROOT, "paper_2002_04989_gb300", "_build", "tune_table.txt")
         t0 = time.perf_counter()
         ctx.eeid_autotune(256, tune_path)
-        extra["autotune_s"] = round(time.perf_counter() - t0, 2)
-        extra["tune_table"] = open(tune_path).read().splitlines()[1:]
+        rec["autotune_s"] = round(time.perf_counter() - t0, 2)
+        rec["tune_table"] = open(tune_path).read().splitlines()[1:]
         mats = inputs.batch4096()
         sizes = [A.shape[0] for A in mats]
-        total = sum(sizes)
         big = torch.empty(sum(n * n for n in sizes), dtype=torch.float64, device=dev)
         outs = torch.empty(sum(n * n for n in sizes), dtype=torch.float64, device=dev)
         probs, off = [], 0
-        host = np.concatenate([A.reshape(-1) for A in mats])
-        big.copy_(torch.from_numpy(host))
+        big.copy_(torch.from_numpy(np.concatenate([A.reshape(-1) for A in mats])))
         for A in mats:
             n = A.shape[0]
-            probs.append({"A": big[off:off + n * n].view(n, n), "out": outs[off:off + n * n].view(n, n)})
+            probs.append({"A": big[off:off + n * n].view(n, n),
+                          "out": outs[off:off + n * n].view(n, n)})
             off += n * n
         units = float(sum(n * n for n in sizes))
         flops = tridiag_flops([(n, n) for n in sizes])
@@ -374,8 +412,8 @@ def run_other(args, world, rank, local):
                 ctx.eeid_components(pr["A"], out=pr["out"], stream=stream)
             flush.fill_(1)
         workload = (f"batch4096: 4096 FP64 symmetric matrices, n log-uniform on [8,256] "
-                    f"(sum n = {total}), thirds GOE / Wishart / Toeplitz(0,1), all components")
-    elif args.workload == "planted4096":
+                    f"(sum n = {sum(sizes)}), thirds GOE / Wishart / Toeplitz(0,1), all components")
+    elif name == "planted4096":
         pl, cols = inputs.planted4096()
         A = torch.from_numpy(pl.A).to(dev)
         out = torch.empty((4096, 256), dtype=torch.float64, device=dev)
@@ -385,9 +423,54 @@ def run_other(args, world, rank, local):
         def step():
             ctx.eeid_components(A, cols=cols, out=out, stream=stream)
             flush.fill_(1)
-        plain_step = None
         workload = ("planted4096: one FP64 n=4096 planted matrix (lam on [-10,10], min gap "
                     "1e-4), all i x 256 seeded columns j (256 minors of size 4095)")
+    elif name == "vectors1024":
+        pl = inputs.planted1024()
+        A = torch.from_numpy(pl.A).to(dev)
+        rows = np.unique(np.r_[0, 511, 1023,
+                               np.random.default_rng(5).choice(1024, 13, replace=False)])
+        out = torch.empty((rows.size, 1024), dtype=torch.float64, device=dev)
+        units = float(rows.size * 1024)
+        flops = None   # depends on the references chosen; filled in below
+
+        def step():
+            ctx.eeid_eigenvectors(A, rows=rows, out=out, stream=stream)
+            flush.fill_(1)
+        phase_timed = False
+        workload = (f"vectors1024: signed eigenvectors (all 1024 components) of the planted "
+                    f"n=1024 matrix for {rows.size} seeded eigen-indices")
+    elif name == "single4002":
+        pl = inputs.planted(4002, inputs.seed_for(inputs.CFG_PLANTED4096, 2), -1.0, 1.0, 1e-4)
+        A = torch.from_numpy(pl.A).to(dev)
+        out = torch.empty((1, 1), dtype=torch.float64, device=dev)
+        units = 1.0
+        flops = tridiag_flops([(4002, 1)])
+        ij = (1234, 2001)
+
+        def step():
+            ctx.eeid_components(A, rows=[ij[0]], cols=[ij[1]], out=out, stream=stream)
+            flush.fill_(1)
+
+        def plain_step():
+            ctx.eeid_set_clusters(False)
+            step()
+            ctx.eeid_set_clusters(True)
+        workload = ("single4002: one component |v_ij|^2 (i=1234, j=2001) of a planted FP64 "
+                    "n=4002 matrix: A and one minor, cluster plan (latency mode); the paper's "
+                    "Table 1 task at n=4002 took 16.78 s on a 4-core Xeon (context only)")
+    elif name == "herm1024":
+        pl = inputs.planted_herm(1024, inputs.seed_for(inputs.CFG_PLANTED1024, 7))
+        A = torch.from_numpy(pl.A).to(dev)
+        out = torch.empty((1024, 1024), dtype=torch.float64, device=dev)
+        units = 1024.0 * 1024
+        flops = 4.0 * tridiag_flops([(1024, 1024)])   # complex: 4 real FMA per complex FMA
+
+        def step():
+            ctx.eeid_components_herm(A, out=out, stream=stream)
+            flush.fill_(1)
+        workload = ("herm1024: one complex Hermitian n=1024 planted-spectrum matrix (unitary Q, "
+                    "lam on [-1,1], min gap 1e-4), full 1024x1024 |v_ij|^2 grid")
     else:
         A = torch.from_numpy(inputs.goe64()).to(dev)
         out = torch.empty((64, 64), dtype=torch.float64, device=dev)
@@ -397,82 +480,100 @@ def run_other(args, world, rank, local):
         def step():
             ctx.eeid_components(A, out=out, stream=stream)
             flush.fill_(1)
-        plain_step = None
         workload = "goe64: one FP64 GOE matrix n=64 (seed 0), all minors, full 64x64 grid"
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     st = ctx.eeid_sync(stream)
-    if args.workload == "planted4096":
-        err = float(np.max(np.abs(out.cpu().numpy() - (pl.Q * pl.Q).T[:, cols])))
-        extra["max_abs_err_vs_QoQ"] = err
-    ctx.eeid_set_timing(True)
+    if name == "planted4096":
+        rec["max_abs_err_vs_QoQ"] = float(np.max(np.abs(out.cpu().numpy() - (pl.Q * pl.Q).T[:, cols])))
+    if name == "single4002":
+        rec["abs_err_vs_QoQ"] = float(abs(out.cpu().numpy()[0, 0] - pl.Q[ij[1], ij[0]] ** 2))
+    if name == "herm1024":
+        rec["max_abs_err_vs_absQ2"] = float(np.max(np.abs(out.cpu().numpy() - (np.abs(pl.Q) ** 2).T)))
+    if name == "vectors1024":
+        ref = pl.Q.T[rows]
+        ref = ref * np.sign(ref[np.arange(rows.size), np.argmax(np.abs(ref), axis=1)])[:, None]
+        rec["max_abs_err_vs_Q"] = float(np.max(np.abs(out.cpu().numpy() - ref)))
+        R = ctx.eeid_vector_refs()
+        rec["references"] = R
+        flops = 4.0 / 3.0 * (1024 ** 3 + (1024 + R * 1023) * 1023 ** 3)
+    ctx.eeid_set_timing(phase_timed)
     clocks = ClockSampler(local)
-    torch.cuda.synchronize()
-    barrier(dist)
     clocks.start()
     l0 = ctx.launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     phases = []
-    e0.record(stream)
-    for _ in range(args.steps):
+
+    def timed_step():
         step()
-        phases.append(ctx.eeid_phase_times())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(dist)
+        if phase_timed:
+            phases.append(ctx.eeid_phase_times())
+    ms = _timed(torch, stream, timed_step, steps)
     clk = clocks.stop()
     launches = ctx.launch_count() - l0
-    ms = e0.elapsed_time(e1)
-    max_ms = max_over_ranks(dist, ms, dev)
-    value = aggregate_value(units, world, args.steps, max_ms)
     ctx.eeid_set_timing(False)
-    phase_avg = {k: round(statistics.mean(ph[k] for ph in phases), 3) for k in phases[0]}
+    phase_avg = ({k: round(statistics.mean(ph[k] for ph in phases), 3) for k in phases[0]}
+                 if phases else None)
     if plain_step is not None:
         plain_step()
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        plain_step()
-        t1.record(stream)
-        torch.cuda.synchronize()
-        extra["plain_one_call_per_matrix"] = {"value": units / (t0.elapsed_time(t1) / 1e3),
-                                              "ms_per_step": t0.elapsed_time(t1)}
-    tri = phase_avg.get("tridiag", 0.0)
-    achieved = flops / (tri / 1e3) / 1e12 if tri > 0 else None
-    peak = FP64_PEAK_GFLOPS / 1e3
+        pm = _timed(torch, stream, plain_step, 1)
+        key = "one_cta_per_matrix" if name == "single4002" else "plain_one_call_per_matrix"
+        rec[key] = {"value": units / (pm / 1e3), "ms_per_step": pm}
+    if phase_avg:
+        roof = alu_roofline(flops, phase_avg.get("tridiag", 0.0),
+                            "k_tridiag (all tridiagonalisations of a step; time = the phase's span)")
+    else:
+        roof = alu_roofline(flops, ms / steps,
+                            "all kernels of the call (reductions of A, its minors and the "
+                            "rotated minors; time = the whole call)")
+    base = {"workload": workload, "value": units * steps / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
+            "components_per_step": units, "roofline": roof, "clocks": clk,
+            "gpu_launches": launches, "phases_ms": phase_avg, "status": st,
+            "timing": "CUDA events on the launching stream; L2 flushed between steps"}
+    base.update(rec)
+    return base
+
+
+def run_other(args, world, rank, local):
+    """The line of one other workload (see workload_record)."""
+    import torch
+
+    from paper_2002_04989_gb300 import eeid
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    ctx = eeid.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    barrier(dist)
+    r = workload_record(args.workload, ctx, dev, stream, args.steps, args.warmup, local)
+    max_ms = max_over_ranks(dist, r["ms_per_step"] * args.steps, dev)
+    value = aggregate_value(r["components_per_step"], world, args.steps, max_ms)
     if rank != 0:
         return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload, "components_per_step_per_gpu": units,
-                       "l2": "flushed between steps (256 MiB write)"},
-            "roofline": {"bound": "alu", "kernel": "k_tridiag (all tridiagonalisations of a step)",
-                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None},
-            "clocks": clk, "gpu_launches": launches, "phases_ms": phase_avg, "status": st}
-    line.update(extra)
+            "config": {"workload": r.pop("workload"),
+                       "components_per_step_per_gpu": r.pop("components_per_step"),
+                       "l2": "flushed between steps (256 MiB write)"}}
+    for k in ("value", "ms_per_step", "steps", "warmup"):
+        r.pop(k)
+    line.update(r)
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serving(args, world, rank, local):
+def serving_record(local, nreq, rates, log=None):
     """Serving: a prefix of the seeded request stream (GOE or planted, n log-uniform
     on [16, 2048], all components or 1-64 random columns) arriving as a Poisson
     process, through the continuous-batching server and, for comparison, through the
-    plain path (one request at a time in arrival order, host buffers)."""
+    plain path (one request at a time in arrival order, host buffers, one context)."""
     import threading
 
     import numpy as np
-    import torch
 
     from paper_2002_04989_gb300 import eeid, inputs
-    torch.cuda.set_device(local)
-    nreq = args.serving_requests
-    rates = [float(r) for r in args.serving_rates.split(",")]
     reqs = [inputs.serving_request(rid) for rid in range(nreq)]
     comps = [r.A.shape[0] * (r.A.shape[0] if r.cols is None else len(r.cols)) for r in reqs]
     work = sum(4.0 / 3.0 * (r.A.shape[0] ** 3 + (r.A.shape[0] if r.cols is None else len(r.cols))
@@ -484,6 +585,8 @@ def run_serving(args, world, rank, local):
 
     for rate in rates:
         arr = inputs.serving_arrivals(nreq, rate)
+        clocks = ClockSampler(local)
+        clocks.start()
         # ---- continuous batching
         lat, done_t = [None] * nreq, [0.0] * nreq
         with eeid.Server(local) as srv:
@@ -509,7 +612,8 @@ def run_serving(args, world, rank, local):
             info = srv.eeid_server_info()
         span = max(done_t) - t0
         served = {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "value": sum(comps) / span,
-                  "makespan_s": span, "batches": info["batches_launched"],
+                  "makespan_s": span, "fp64_tflops": work / span / 1e12,
+                  "batches": info["batches_launched"],
                   "max_overlapping_batches": info["max_overlapping_batches"]}
         # ---- plain: one request at a time, arrival order
         ctx = eeid.Context(local)
@@ -523,35 +627,70 @@ def run_serving(args, world, rank, local):
             lat_p.append(1e3 * (time.perf_counter() - (t0 + arr[k])))
         span_p = time.perf_counter() - t0
         ctx.close()
+        clk = clocks.stop()
         plain = {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99), "value": sum(comps) / span_p,
-                 "makespan_s": span_p}
-        results.append({"rate_per_s": rate, "served": served, "plain": plain})
-        print(json.dumps({"rate": rate, "served": served, "plain": plain}), file=sys.stderr, flush=True)
+                 "makespan_s": span_p, "fp64_tflops": work / span_p / 1e12}
+        results.append({"rate_per_s": rate, "served": served, "plain": plain, "clocks": clk})
+        if log is not None:
+            print(json.dumps({"rate": rate, "served": served, "plain": plain}), file=log, flush=True)
+    return {"workload": (f"serving: first {nreq} requests of the seeded stream (GOE or planted "
+                         f"50:50, n log-uniform on [16,2048], all or 1-64 columns), Poisson "
+                         f"arrivals"),
+            "requests": nreq, "components": sum(comps), "tridiag_flops": work,
+            "timing": "host wall clock from each arrival to its results in host memory",
+            "sweep": results}
+
+
+def run_serving(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    rates = [float(r) for r in args.serving_rates.split(",")]
+    rec = serving_record(local, args.serving_requests, rates, log=sys.stderr)
     if rank != 0:
         return 0
-    best = max(results, key=lambda x: x["served"]["value"])
-    line = {"metric": METRIC + "; serving p50/p99 latency vs plain GPU path", "value": best["served"]["value"],
-            "unit": UNIT, "n_gpus": 1, "steps": len(rates), "warmup": 0, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": (f"serving: first {nreq} requests of the seeded stream (GOE or "
-                                    f"planted 50:50, n log-uniform on [16,2048], all or 1-64 "
-                                    f"columns), Poisson arrivals"),
-                       "requests": nreq, "components": sum(comps), "tridiag_flops": work},
-            "sweep": results}
+    best = max(rec["sweep"], key=lambda x: x["served"]["value"])
+    line = {"metric": METRIC + "; serving p50/p99 latency vs plain GPU path",
+            "value": best["served"]["value"], "unit": UNIT, "n_gpus": 1, "steps": len(rates),
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": rec["workload"], "requests": rec["requests"],
+                       "components": rec["components"], "tridiag_flops": rec["tridiag_flops"]},
+            "sweep": rec["sweep"]}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def run_profile_case(case: str) -> int:
-    """Small, self-checking case sized for an ncu capture (a few GB on the device)."""
+    """Small, self-checking cases sized for an ncu capture (a few GB on the device):
+    tridiag152 / tridiag304 = A plus the first 151 / 303 minors of the planted n=1024
+    matrix (one / two CTAs per SM), called twice (its k_bisect, k_denominators and
+    k_identity launches are the ones captured for those kernels); batch256 = the
+    matrices of the uneven batch with n in (192, 256] (316 of them) in one batched call
+    with the autotuned variants, graphs off, called twice."""
     import numpy as np
     import torch
 
     from paper_2002_04989_gb300 import eeid, inputs
+    ctx = eeid.Context(0)
+    if case == "batch256":
+        tune_path = os.path.join(ROOT, "paper_2002_04989_gb300", "_build", "tune_table.txt")
+        ctx.eeid_autotune(256, tune_path)
+        ctx.eeid_set_graphs(False)
+        mats = [A for A in inputs.batch4096() if 192 < A.shape[0] <= 256]
+        probs = []
+        for A in mats:
+            n = A.shape[0]
+            probs.append({"A": torch.from_numpy(A).cuda(),
+                          "out": torch.empty((n, n), dtype=torch.float64, device="cuda")})
+        for _ in range(2):
+            ctx.eeid_components_batched(probs)
+            ctx.eeid_sync()
+        worst = max(float(np.max(np.abs(pr["out"].sum(dim=0).cpu().numpy() - 1.0))) for pr in probs)
+        print(f"{case}: {len(mats)} matrices, worst column-sum deviation {worst:.3e}")
+        return 0 if worst <= 1e-9 else 1
     p = inputs.planted1024()
     A = torch.from_numpy(p.A).cuda()
     cols = np.arange(151 if case == "tridiag152" else 303)
-    ctx = eeid.Context(0)
     for _ in range(2):
         out = ctx.eeid_components(A, cols=cols)
         ctx.eeid_sync()
@@ -568,8 +707,10 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other workloads' records after the headline")
     ap.add_argument("--workload", choices=("planted1024", "batch4096", "planted4096", "goe64",
-                                           "serving"),
+                                           "vectors1024", "herm1024", "single4002", "serving"),
                     default="planted1024",
                     help="planted1024 (default, the headline line); the others print a line "
                          "of the same shape for the other workloads")
@@ -577,7 +718,7 @@ def main(argv=None):
                     help="serving: length of the prefix of the seeded request stream")
     ap.add_argument("--serving-rates", default="0.5,1,2",
                     help="serving: comma-separated Poisson arrival rates (requests/s)")
-    ap.add_argument("--profile-case", choices=("tridiag152", "tridiag304"), default=None,
+    ap.add_argument("--profile-case", choices=("tridiag152", "tridiag304", "batch256"), default=None,
                     help="run only a small case for an ncu capture and exit: tridiag152 / "
                          "tridiag304 = A plus the first 151 / 303 minors of the planted "
                          "n=1024 matrix (one / two CTAs per SM), called twice")

@@ -32,6 +32,9 @@
  *  - A context's workspace is shared by its calls: issue the calls of one
  *    context on one stream (or order them yourself).  Contexts are not
  *    thread-safe; use one per host thread.
+ *  - Deferred status is kept per stream: eeid_sync(ctx, s) returns and clears
+ *    only what the context's calls on stream s raised (63 streams per context
+ *    have a word of their own; further streams share one).
  *  - Status codes: negative = error (nothing, or only part, was enqueued),
  *    positive = warning (results written).  eeid_last_error() gives a message.
  */
@@ -76,9 +79,10 @@ void eeid_ctx_destroy(eeid_ctx* ctx);
 /* Message for the last error or warning raised on the calling host thread. */
 const char* eeid_last_error(void);
 
-/* Wait for all work enqueued on `stream` and return the worst deferred status of
- * the context's calls since the previous eeid_sync (errors before warnings), then
- * clear it. */
+/* Return the worst deferred status of the context's calls on `stream` since the
+ * previous eeid_sync on that stream (errors before warnings) and clear it.  The status
+ * word is read and cleared on `stream` itself, after the calls, and the call then waits
+ * for the stream; other streams' warnings are left for their own eeid_sync. */
 eeid_status eeid_sync(eeid_ctx* ctx, void* stream);
 
 /* Eigenvalues lam_1(A) <= ... <= lam_n(A) of A (Sec. 2: the first input of Eq. 1).
@@ -106,7 +110,8 @@ eeid_status eeid_components(eeid_ctx* ctx, const double* dA, int64_t lda, int64_
                             int64_t ncols, double* d_out, double* d_lambda_opt, void* stream);
 
 /* eeid_components on HOST buffers: copies hA (host, n x lda doubles, pinned or
- * pageable) to the context's device workspace, runs the path on `stream`, copies
+ * pageable) into a device buffer the context keeps between calls (it is allocated
+ * only when a call needs more than the last), runs the path on `stream`, copies
  * the nrows x ncols grid back into h_out (and the eigenvalues into h_lambda_opt),
  * and synchronises the stream.  Returns the call's final status (warnings
  * included).  Same index conventions as eeid_components. */
@@ -136,6 +141,21 @@ eeid_status eeid_components_host(eeid_ctx* ctx, const double* hA, int64_t lda, i
 eeid_status eeid_eigenvectors(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n,
                               const int64_t* h_rows, int64_t nrows, double* d_vec,
                               double* d_lambda_opt, void* stream);
+
+/* Eq. 1 for a complex Hermitian A (Sec. 2 states the identity for Hermitian matrices):
+ * d_out[r*ncols + c] = |v_ij|^2 for i = h_rows[r], j = h_cols[c], as eeid_components.
+ * dA: device, row-major, interleaved (re, im) doubles, leading dimension lda >= n in
+ * complex elements (16 bytes each); only the lower triangle is read, and the imaginary
+ * parts of the diagonal are ignored (a Hermitian diagonal is real).  A and its minors are
+ * reduced by unitary Householder reflections to real symmetric tridiagonals; bisection and
+ * the identity are those of the real path.  n <= 2048 (the complex reduction keeps three
+ * vectors of 16-byte entries in shared memory); larger n gives EEID_ERR_INVALID.
+ * d_lambda_opt: optional device buffer of n doubles for the eigenvalues of A.  Same index
+ * conventions, no-op cases and deferred warnings as eeid_components. */
+eeid_status eeid_components_herm(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n,
+                                 const int64_t* h_rows, int64_t nrows, const int64_t* h_cols,
+                                 int64_t ncols, double* d_out, double* d_lambda_opt,
+                                 void* stream);
 
 /* One problem of a batch: the arguments of eeid_components.  h_rows / h_cols NULL
  * mean "all" (nrows / ncols = n). */
@@ -175,6 +195,16 @@ eeid_status eeid_set_graphs(eeid_ctx* ctx, int enable);
  * same either way; with the plan on, the phase times of eeid_phase_times may
  * overlap. */
 eeid_status eeid_set_overlap(eeid_ctx* ctx, int enable);
+
+/* Enable (default) or disable the cluster plan (latency mode).  When a call has few
+ * Householder reductions (at most half as many as the device has SMs: one or a few
+ * components, a few columns, or the eigenvalues of one large A -- the single-component
+ * tasks of the paper's Table 1) of matrices with m >= 384, each reduction runs on a
+ * thread-block cluster of up to 16 CTAs on as many SMs instead of on one CTA: the tiles
+ * of every column step are split over the cluster, partial sums stay in the matrix's
+ * workspace slot and the step vectors are exchanged through distributed shared memory.
+ * Results are bitwise the same either way. */
+eeid_status eeid_set_clusters(eeid_ctx* ctx, int enable);
 
 /* Number of kernel launches the context has enqueued so far (for accounting). */
 int64_t eeid_launch_count(const eeid_ctx* ctx);

@@ -16,6 +16,14 @@
 
 namespace eeid {
 int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m);
+cudaError_t launch_tridiag_cluster(int warps, int nclusters, int csize, const TridiagLaunch& L,
+                                   cudaStream_t s);
+int tridiag_max_active_clusters(int warps, int csize, int max_m);
+size_t tridiag_herm_slot_doubles(int max_m);
+size_t tridiag_herm_smem_bytes(int max_m, int warps);
+cudaError_t launch_tridiag_herm(int warps, int grid, const TridiagLaunch& L, cudaStream_t s);
+cudaError_t preload_tridiag_herm();
+int tridiag_herm_blocks_per_sm(int warps, int max_m);
 cudaError_t preload_vectors();
 size_t pick_refs_smem_bytes(int nrows, int n);
 cudaError_t launch_pick_refs(const double* g, int nrows, int n, int* refs, int* row_ref,
@@ -61,6 +69,7 @@ eeid_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr size_t kAlign = 256;
+constexpr int kStatusSlots = 64;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 }  // namespace
@@ -71,7 +80,16 @@ struct eeid_ctx {
   size_t budget = 0;
   char* ws = nullptr;
   size_t ws_cap = 0;
+  // Device status words, one per stream the context has run on (slot 0: internal work
+  // and streams beyond the table), so eeid_sync(stream) reads and clears only the word of
+  // that stream's calls.  h_status: pinned copies read back on the stream itself.
   unsigned* d_status = nullptr;
+  unsigned* h_status = nullptr;
+  std::vector<cudaStream_t> status_streams;   // slot s + 1 belongs to status_streams[s]
+  // eeid_components_host: device copies of A, the grid and the eigenvalues, kept for
+  // the next call (no allocation per call once it is large enough).
+  char* host_call_buf = nullptr;
+  size_t host_call_cap = 0;
   char* h_stage = nullptr;
   size_t h_stage_cap = 0;
   cudaEvent_t stage_ev = nullptr;
@@ -102,6 +120,8 @@ struct eeid_ctx {
   bool round_launches = false;
   // SMs the persistent reductions leave free (serving: room for a second batch).
   int sm_reserve = 0;
+  // Cluster plan for groups of few large reductions (see cluster_size_for).
+  bool clusters_enabled = true;
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   bool timing = false;
@@ -128,7 +148,9 @@ namespace {
 struct TriCfg {
   bool smem;
   int warps;
+  bool herm = false;   // complex Hermitian reduction (its own kernel, global slots)
 };
+constexpr int kHermMaxM = 2048;   // largest complex Hermitian matrix (shared-memory vectors)
 constexpr size_t kMaxSmemPerBlock = 232448;  // opt-in shared memory per CTA on sm_103a
 
 TriCfg tri_cfg_default(int m) {
@@ -140,7 +162,11 @@ TriCfg tri_cfg_default(int m) {
   if (tridiag_smem_bytes(false, m, 12) <= kMaxSmemPerBlock) return {false, 12};
   return {false, 8};
 }
-inline int cfg_key(const TriCfg& c) { return (c.smem ? 0 : 32) + c.warps; }
+inline int cfg_key(const TriCfg& c) { return c.herm ? 96 + c.warps : (c.smem ? 0 : 32) + c.warps; }
+
+TriCfg herm_cfg(int m) {
+  return {false, tridiag_herm_smem_bytes(m, 8) <= kMaxSmemPerBlock ? 8 : 4, true};
+}
 
 bool cfg_supported(bool smem, int warps, int m) {
   bool ok;
@@ -166,6 +192,8 @@ struct Problem {
   // Eigenvalues of A computed earlier on the same stream: A is not reduced or bisected
   // again, and these seed the minors' brackets and the denominators.
   const double* lam_in = nullptr;
+  // Complex Hermitian A (interleaved re/im doubles, lda in complex elements).
+  bool herm = false;
 };
 
 enum Mode { MODE_EIGVALS, MODE_MINORS, MODE_COMPONENTS };
@@ -276,6 +304,15 @@ eeid_status ensure_aux(eeid_ctx* ctx) {
   return EEID_OK;
 }
 
+// Status slot of a stream (assigned at its first use; slot 0 when the table is full).
+int status_slot(eeid_ctx* ctx, cudaStream_t s, bool assign) {
+  for (size_t k = 0; k < ctx->status_streams.size(); ++k)
+    if (ctx->status_streams[k] == s) return (int)k + 1;
+  if (!assign || (int)ctx->status_streams.size() + 1 >= kStatusSlots) return 0;
+  ctx->status_streams.push_back(s);
+  return (int)ctx->status_streams.size();
+}
+
 TriCfg tri_cfg(const eeid_ctx* ctx, int m) {
   for (auto it = ctx->rules.rbegin(); it != ctx->rules.rend(); ++it)
     if (m >= it->lo && m <= it->hi && cfg_supported(it->smem, it->warps, m))
@@ -292,6 +329,7 @@ bool rule_covers(const eeid_ctx* ctx, int m) {
 
 
 int blocks_per_sm(eeid_ctx* ctx, const TriCfg& c, int max_m) {
+  if (c.herm) return std::max(1, tridiag_herm_blocks_per_sm(c.warps, max_m));
   int& cache = ctx->occ_cache[c.smem ? 0 : 1][c.warps];
   int& cm = ctx->occ_m[c.smem ? 0 : 1][c.warps];
   if (cache == 0 || cm != max_m) {
@@ -316,6 +354,7 @@ std::string batch_key(const std::vector<Problem>& probs, bool timing, int rules_
     put(&P.out, sizeof P.out);
     put(&P.lam_user, sizeof P.lam_user);
     put(&P.rot, sizeof P.rot);
+    put(&P.herm, sizeof P.herm);
     put(&P.lam_in, sizeof P.lam_in);
     const int nr = (int)P.rows.size(), nc = (int)P.cols.size();
     const char flags = (char)((P.all_rows ? 1 : 0) | (P.all_cols ? 2 : 0));
@@ -337,6 +376,7 @@ constexpr size_t kMaxGraphs = 8;
 eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStream_t stream,
                 eeid_ctx::GraphEntry* ge = nullptr) {
   EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  unsigned* const status_word = ctx->d_status + status_slot(ctx, stream, true);
   // ---- task lists (host)
   struct TriRef { int prob; int col; int m; };  // col = -1: A itself
   std::vector<TriRef> tri;
@@ -373,28 +413,49 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     }
   }
   // tridiagonalisation groups (one persistent launch per configuration)
-  std::vector<std::vector<int>> groups(64);
-  for (size_t t = 0; t < tri.size(); ++t) groups[cfg_key(tri_cfg(ctx, tri[t].m))].push_back((int)t);
+  std::vector<std::vector<int>> groups(128);
+  for (size_t t = 0; t < tri.size(); ++t)
+    groups[cfg_key(probs[tri[t].prob].herm ? herm_cfg(tri[t].m) : tri_cfg(ctx, tri[t].m))]
+        .push_back((int)t);
   struct GroupPlan { TriCfg cfg; int max_m; int grid; int nchunks; size_t task_off, counter_off,
-                     work_off; size_t slot; std::vector<int> idx; };
+                     work_off; size_t slot; std::vector<int> idx; int csize = 0; };
   std::vector<GroupPlan> gplans;
-  for (int key = 0; key < 64; ++key) {
+  for (int key = 0; key < 128; ++key) {
     if (groups[key].empty()) continue;
     GroupPlan g;
     g.idx = groups[key];
     std::stable_sort(g.idx.begin(), g.idx.end(),
                      [&](int a, int b) { return tri[a].m > tri[b].m; });  // cost-sorted
     g.max_m = tri[g.idx[0]].m;
-    g.cfg = tri_cfg(ctx, g.max_m);
+    g.cfg = key >= 96 ? herm_cfg(g.max_m) : tri_cfg(ctx, g.max_m);
     const int bps = blocks_per_sm(ctx, g.cfg, g.max_m);
     const int sms_used = std::max(1, ctx->sms - ctx->sm_reserve);
     g.grid = (int)std::min<int64_t>((int64_t)g.idx.size(), (int64_t)sms_used * bps);
-    g.slot = g.cfg.smem ? 0 : tridiag_global_slot_doubles(g.max_m);
+    g.slot = g.cfg.herm ? tridiag_herm_slot_doubles(g.max_m)
+             : g.cfg.smem ? 0 : tridiag_global_slot_doubles(g.max_m);
     g.work_off = 0;  // assigned after the rest of the layout (see below)
     g.task_off = meta.take(sizeof(TridiagTask) * g.idx.size());
     g.nchunks = ctx->round_launches ? (int)((g.idx.size() + g.grid - 1) / g.grid) : 1;
     g.counter_off = meta.take(sizeof(int) * g.nchunks);
     gplans.push_back(std::move(g));
+  }
+  // Cluster plan: a single group of few large reductions runs one cluster of csize CTAs
+  // per matrix (one round; each cluster works in one global slot).  Results are
+  // bitwise those of the one-CTA global variant.
+  if (ctx->clusters_enabled && !ctx->round_launches && gplans.size() == 1 &&
+      !gplans[0].cfg.smem && !gplans[0].cfg.herm && !rule_covers(ctx, gplans[0].max_m)) {
+    GroupPlan& g = gplans[0];
+    const int nt = (int)g.idx.size();
+    int c = cluster_size_for(nt, std::max(1, ctx->sms - ctx->sm_reserve), g.max_m);
+    int w = 0;
+    for (int cand : {16, 12, 8})
+      if (!w && tridiag_smem_bytes(false, g.max_m, cand) <= kMaxSmemPerBlock) w = cand;
+    while (c >= 2 && w && tridiag_max_active_clusters(w, c, g.max_m) < nt) c /= 2;
+    if (c >= 2 && w) {
+      g.csize = c;
+      g.cfg = {false, w};
+      g.grid = nt;   // clusters (= slots)
+    }
   }
   // Tail overlap.  One group of near-equal tasks (sizes within 1) in more than one
   // round leaves grid - r CTAs idle through its last round (r = tasks mod grid).  Then
@@ -412,7 +473,8 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   TriCfg tail_cfg{false, 0};
   size_t counter2_off = 0;
   std::vector<char> in_tail(tri.size(), 0);
-  if (ctx->overlap_enabled && !ctx->round_launches && gplans.size() == 1 && mode != MODE_EIGVALS) {
+  if (ctx->overlap_enabled && !ctx->round_launches && gplans.size() == 1 && mode != MODE_EIGVALS &&
+      gplans[0].csize == 0 && !gplans[0].cfg.herm) {
     GroupPlan& g = gplans[0];
     const int nt = (int)g.idx.size();
     const bool uniform = tri[g.idx.back()].m + 1 >= tri[g.idx.front()].m;
@@ -498,6 +560,12 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
       const double scale = (double)(ctx->budget - fixed) / (double)slots_total;
       for (auto& g : gplans) {
         if (g.cfg.smem) continue;
+        if (g.csize) {   // fewer slots than matrices: back to one CTA per matrix
+          g.csize = 0;
+          g.cfg = tri_cfg(ctx, g.max_m);
+          g.slot = tridiag_global_slot_doubles(g.max_m);
+          g.grid = std::min<int>((int)g.idx.size(), ctx->sms * blocks_per_sm(ctx, g.cfg, g.max_m));
+        }
         const int ng = (int)((double)g.grid * scale);
         if (ng < 1)
           return fail(EEID_ERR_NOMEM, "one working slot (%zu bytes) does not fit the HBM budget",
@@ -599,7 +667,11 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     L.work = g.cfg.smem ? nullptr : D(g.work_off);
     L.work_stride = (int64_t)g.slot;
     L.max_m = g.max_m;
-    L.status = ctx->d_status;
+    L.status = status_word;
+    auto launch_group = [&](int grid, const TridiagLaunch& LL, cudaStream_t on) {
+      return g.cfg.herm ? launch_tridiag_herm(g.cfg.warps, grid, LL, on)
+                        : launch_tridiag(g.cfg.smem, g.cfg.warps, grid, LL, on);
+    };
     if (g.nchunks > 1) {
       // round launches: chunk c takes tasks [c*chunk, ...) with its own counter
       const int total = L.ntasks, chunk = (total + g.nchunks - 1) / g.nchunks;
@@ -610,13 +682,18 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
         L.tasks = t0 + a;
         L.ntasks = b - a;
         L.counter = (int*)(ws + g.counter_off) + c;
-        EEID_CK(launch_tridiag(g.cfg.smem, g.cfg.warps, std::min(g.grid, b - a), L, stream),
-                "tridiag launch");
+        EEID_CK(launch_group(std::min(g.grid, b - a), L, stream), "tridiag launch");
         ctx->launches++;
       }
       continue;
     }
-    EEID_CK(launch_tridiag(g.cfg.smem, g.cfg.warps, g.grid, L, stream), "tridiag launch");
+    if (g.csize) {
+      EEID_CK(launch_tridiag_cluster(g.cfg.warps, g.grid, g.csize, L, stream),
+              "tridiag cluster launch");
+      ctx->launches++;
+      continue;
+    }
+    EEID_CK(launch_group(g.grid, L, stream), "tridiag launch");
     ctx->launches++;
     if (tail_at > 0) {
       // the tail: same slots (the first launch is done with them), its own counter
@@ -640,14 +717,14 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   if (!items_a.empty()) {
     EEID_CK(mark(EEID_PHASE_BISECT_A, 0, stream), "event");
     EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bia_off), (int)items_a.size(), mm_a,
-                          ctx->d_status, stream), "bisect(A) launch");
+                          status_word, stream), "bisect(A) launch");
     ctx->launches++;
     EEID_CK(mark(EEID_PHASE_BISECT_A, 1, stream), "event");
   }
   if (mode == MODE_COMPONENTS) {
     EEID_CK(mark(EEID_PHASE_DENOMINATORS, 0, stream), "event");
     EEID_CK(launch_denominators((const DenomTask*)(ws + dt_off), (int)probs.size(), max_n,
-                                ctx->d_status, stream), "denominators launch");
+                                status_word, stream), "denominators launch");
     ctx->launches++;
     EEID_CK(mark(EEID_PHASE_DENOMINATORS, 1, stream), "event");
   }
@@ -655,13 +732,13 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     EEID_CK(mark(EEID_PHASE_BISECT_MINORS, 0, stream), "event");
     if (!items_m.empty()) {
       EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bim_off), (int)items_m.size(), mm_m,
-                            ctx->d_status, stream), "bisect(minors) launch");
+                            status_word, stream), "bisect(minors) launch");
       ctx->launches++;
     }
     if (tail_at > 0) EEID_CK(cudaStreamWaitEvent(stream, ctx->join_ev, 0), "join wait");
     if (!items_m2.empty()) {
       EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bim2_off), (int)items_m2.size(), mm_m2,
-                            ctx->d_status, stream), "bisect(tail minors) launch");
+                            status_word, stream), "bisect(tail minors) launch");
       ctx->launches++;
     }
     EEID_CK(mark(EEID_PHASE_BISECT_MINORS, 1, stream), "event");
@@ -738,14 +815,16 @@ eeid_status eeid_ctx_create(int device, size_t hbm_budget_bytes, eeid_ctx** out)
   c->device = device;
   c->sms = prop.multiProcessorCount;
   c->budget = hbm_budget_bytes ? hbm_budget_bytes : fr / 2;
-  e = cudaMalloc((void**)&c->d_status, 256);
-  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 256);
+  e = cudaMalloc((void**)&c->d_status, sizeof(unsigned) * kStatusSlots);
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned) * kStatusSlots);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_status, sizeof(unsigned) * kStatusSlots);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
   // every kernel loaded now, not at its first launch (see preload_tridiag)
   if (e == cudaSuccess) e = preload_tridiag();
   if (e == cudaSuccess) e = preload_bisect();
   if (e == cudaSuccess) e = preload_identity();
   if (e == cudaSuccess) e = preload_vectors();
+  if (e == cudaSuccess) e = preload_tridiag_herm();
   if (e != cudaSuccess) {
     eeid_ctx_destroy(c);
     return cuda_fail(e, "context setup");
@@ -765,6 +844,8 @@ void eeid_ctx_destroy(eeid_ctx* ctx) {
   if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->host_call_buf) cudaFree(ctx->host_call_buf);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
   if (ctx->vbuf) cudaFree(ctx->vbuf);
@@ -961,6 +1042,13 @@ eeid_status set_sm_reserve(eeid_ctx* ctx, int sms) {
 
 extern "C" {
 
+eeid_status eeid_set_clusters(eeid_ctx* ctx, int enable) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  ctx->clusters_enabled = enable != 0;   // part of the graph key: no graph goes stale
+  return EEID_OK;
+}
+
 eeid_status eeid_set_overlap(eeid_ctx* ctx, int enable) {
   eeid_status st = check_ctx(ctx);
   if (st != EEID_OK) return st;
@@ -1010,10 +1098,15 @@ eeid_status eeid_sync(eeid_ctx* ctx, void* stream) {
   eeid_status st = check_ctx(ctx);
   if (st != EEID_OK) return st;
   EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  EEID_CK(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
-  unsigned bits = 0;
-  EEID_CK(cudaMemcpy(&bits, ctx->d_status, sizeof bits, cudaMemcpyDeviceToHost), "status read");
-  EEID_CK(cudaMemset(ctx->d_status, 0, sizeof bits), "status clear");
+  cudaStream_t s = (cudaStream_t)stream;
+  // a stream this context never ran on, or one beyond the table, has the shared word
+  const int slot = status_slot(ctx, s, false);
+  // read and clear this stream's word in its own order, then wait for the stream
+  EEID_CK(cudaMemcpyAsync(ctx->h_status + slot, ctx->d_status + slot, sizeof(unsigned),
+                          cudaMemcpyDeviceToHost, s), "status read");
+  EEID_CK(cudaMemsetAsync(ctx->d_status + slot, 0, sizeof(unsigned), s), "status clear");
+  EEID_CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  const unsigned bits = ctx->h_status[slot];
   if (bits & ST_BAD_TASK) return fail(EEID_ERR_INVALID, "a kernel met a task beyond its size limit");
   if (bits & ST_DEGENERATE)
     return fail(EEID_WARN_DEGENERATE, "equal eigenvalues of A: Eq. 1 is 0/0; rows set to NaN");
@@ -1098,8 +1191,11 @@ eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* in, int64
   EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   if (!ctx->graphs_enabled) return run(ctx, probs, MODE_COMPONENTS, s);
-  std::string key = batch_key(probs, ctx->timing, ctx->rules_version,
-                              (ctx->overlap_enabled ? 1 : 0) | (ctx->round_launches ? 2 : 0));
+  // the graph bakes in the status word of the stream it was captured for
+  const int slot = status_slot(ctx, s, true);
+  std::string key = std::to_string(slot) + ":" + batch_key(probs, ctx->timing, ctx->rules_version,
+                              (ctx->overlap_enabled ? 1 : 0) | (ctx->round_launches ? 2 : 0) |
+                                  (ctx->clusters_enabled ? 4 : 0));
   for (auto& g : ctx->graphs) {
     if (g.key == key) {
       g.last_use = ++ctx->graph_clock;
@@ -1151,15 +1247,29 @@ eeid_status eeid_components_host(eeid_ctx* ctx, const double* hA, int64_t lda, i
   const int64_t nr = h_rows ? nrows : n, nc = h_cols ? ncols : n;
   if (n == 0 || nr == 0 || nc == 0) return EEID_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  // Device staging for A, the grid and the eigenvalues lives in a separate
-  // allocation owned by this call (the context workspace is re-planned by run()).
+  // Device copies of A, the grid and the eigenvalues live in a context-owned buffer kept
+  // between calls (the context workspace is re-planned by run()); it grows only when a
+  // call needs more, so repeated calls of one size allocate nothing.
   const size_t a_bytes = sizeof(double) * (size_t)n * lda;
   const size_t o_bytes = sizeof(double) * (size_t)nr * nc;
   const size_t l_bytes = sizeof(double) * (size_t)n;
-  char* buf = nullptr;
+  const size_t need = align_up(a_bytes) + align_up(o_bytes) + align_up(l_bytes);
   EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  EEID_CK(cudaMallocAsync((void**)&buf, align_up(a_bytes) + align_up(o_bytes) + align_up(l_bytes), s),
-          "cudaMallocAsync(host-call staging)");
+  if (need > ctx->host_call_cap) {
+    if (ctx->host_call_buf) {
+      cudaError_t e0 = cudaFree(ctx->host_call_buf);   // synchronises the device
+      ctx->host_call_buf = nullptr;
+      ctx->host_call_cap = 0;
+      if (e0 != cudaSuccess) return cuda_fail(e0, "cudaFree(host-call buffer)");
+    }
+    cudaError_t e0 = cudaMalloc((void**)&ctx->host_call_buf, need);
+    if (e0 != cudaSuccess) {
+      cudaGetLastError();
+      return fail(EEID_ERR_NOMEM, "cudaMalloc(%zu) for the host-call buffer failed", need);
+    }
+    ctx->host_call_cap = need;
+  }
+  char* buf = ctx->host_call_buf;
   double* dA = (double*)buf;
   double* dO = (double*)(buf + align_up(a_bytes));
   double* dL = (double*)(buf + align_up(a_bytes) + align_up(o_bytes));
@@ -1173,7 +1283,6 @@ eeid_status eeid_components_host(eeid_ctx* ctx, const double* hA, int64_t lda, i
         e = cudaMemcpyAsync(h_lambda_opt, dL, l_bytes, cudaMemcpyDeviceToHost, s);
     }
   }
-  cudaFreeAsync(buf, s);
   if (e != cudaSuccess) return cuda_fail(e, "host-buffer copy");
   if (st != EEID_OK) {
     cudaStreamSynchronize(s);
@@ -1294,6 +1403,24 @@ eeid_status eeid_eigenvectors(eeid_ctx* ctx, const double* dA, int64_t lda, int6
   EEID_CK(launch_signed(vb + s_off, NR, N, s), "signed launch");
   ctx->launches++;
   return EEID_OK;
+}
+
+
+eeid_status eeid_components_herm(eeid_ctx* ctx, const double* dA, int64_t lda, int64_t n,
+                                 const int64_t* h_rows, int64_t nrows, const int64_t* h_cols,
+                                 int64_t ncols, double* d_out, double* d_lambda_opt,
+                                 void* stream) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  if (n > kHermMaxM)
+    return fail(EEID_ERR_INVALID, "n = %lld exceeds the Hermitian limit %d", (long long)n, kHermMaxM);
+  std::vector<Problem> probs(1);
+  st = make_component_problem(dA, lda, n, h_rows, nrows, h_cols, ncols, d_out, d_lambda_opt,
+                              probs[0]);
+  if (st != EEID_OK) return st;
+  probs[0].herm = true;
+  if (probs[0].n == 0) return EEID_OK;
+  return run(ctx, probs, MODE_COMPONENTS, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -68,6 +68,23 @@ inline RoundPlan plan_rounds(int nt, int grid, int sms, bool wide, int blocks8, 
   return p;
 }
 
+// Cluster plan of one group of reductions: when the group has at most half as many
+// matrices as the device has SMs (a few components, or the eigenvalues of one large A,
+// the paper's Table 1 tasks), one thread-block cluster of C CTAs reduces each matrix
+// instead of one CTA, so the whole group runs in one round on up to C times the SMs.
+// C is the largest power of two with nt * C <= sms, at most the cluster limit (16);
+// 0 = no cluster plan (too many matrices, or matrices below min_m, whose per-step
+// serial phases would dominate a split pass).  The caller then halves C while the
+// device cannot hold nt such clusters at once.
+constexpr int kClusterMaxCtas = 16;
+constexpr int kClusterMinM = 384;
+inline int cluster_size_for(int nt, int sms, int max_m, int min_m = kClusterMinM) {
+  if (nt < 1 || max_m < min_m || 2 * nt > sms) return 0;
+  int c = 1;
+  while (2 * c <= kClusterMaxCtas && nt * 2 * c <= sms) c *= 2;
+  return c >= 2 ? c : 0;
+}
+
 // Serving: cost band of a request, from n^3 (columns + 1), which is proportional to its
 // Householder work (the reductions dominate).  Everything below kTinyCost is band 0,
 // then one band per factor of 8.  A batch holds requests of one band only.

@@ -30,7 +30,10 @@
 //                 small m), tiles are staged through a per-warp shared buffer.
 #include "internal.cuh"
 
+#include <cooperative_groups.h>
 #include <cstdio>
+
+namespace cg = cooperative_groups;
 
 namespace eeid {
 namespace {
@@ -236,17 +239,44 @@ __host__ __device__ inline Layout make_layout(bool smem, int max_m) {
   return L;
 }
 
+// Barrier of the CTA, or of the whole cluster with its global-memory writes (the
+// working slot's tiles and partial sums) made visible to the other CTAs first.
+template <bool CL>
+__device__ __forceinline__ void block_or_cluster_sync() {
+  if constexpr (CL) {
+    __threadfence();
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+}
+
 // Minimum resident CTAs per SM the register allocation must allow.
 template <bool SMEM, int W>
 struct MinBlocks {
   static constexpr int value = (W >= 12) ? 1 : (W >= 8) ? 2 : (SMEM && W <= 2) ? 8 : 4;
 };
 
-template <bool SMEM, int W>
+// CL = true: the cluster variant (global-slot path only).  One thread-block cluster of C
+// CTAs reduces one matrix: the tiles of each step's fused pass are split over the C*W
+// warps of the cluster, every tile keeps its partial sums in the cluster's global slot
+// as in the one-CTA variant, and each CTA sums its share of the elements in Phase E in
+// the same tile order and writes them into every CTA's shared copy of w (distributed
+// shared memory).  The serial phases (A-C, gamma, F) run redundantly in every CTA on
+// identical data.  So the results are bitwise those of the one-CTA global variant.
+template <bool SMEM, int W, bool CL = false>
 __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag(TridiagLaunch P) {
   extern __shared__ __align__(16) double sm[];
   constexpr int NT = W * 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // cluster geometry (1 CTA and rank 0 without clusters)
+  int crank = 0, csize = 1;
+  if constexpr (CL) {
+    cg::cluster_group cluster = cg::this_cluster();
+    crank = (int)cluster.block_rank();
+    csize = (int)cluster.num_blocks();
+  }
+  const int gwarp = crank * W + warp, GW = csize * W;   // warp index within the cluster
   const Layout Ly = make_layout(SMEM, P.max_m);
   const int64_t ld = Ly.ld;
   const int nbmax = Ly.nbmax;
@@ -268,7 +298,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
     tpart = S + (size_t)P.max_m * ld;
     upart = tpart + (size_t)nbmax * nbmax * 32;
   } else {
-    double* slot = P.work + (size_t)blockIdx.x * P.work_stride;
+    double* slot = P.work + (size_t)(blockIdx.x / csize) * P.work_stride;
     S = slot;
     tpart = S + (size_t)P.max_m * ld;
     upart = tpart + (size_t)nbmax * nbmax * 32;
@@ -277,10 +307,21 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
   __shared__ int s_task;
 
   for (;;) {
-    if (tid == 0) s_task = atomicAdd(P.counter, 1);
-    __syncthreads();
+    if constexpr (CL) {
+      // rank 0 takes the cluster's next task and hands it to every CTA
+      cg::cluster_group cluster = cg::this_cluster();
+      if (crank == 0 && tid == 0) {
+        const int t0 = atomicAdd(P.counter, 1);
+        for (int r = 0; r < csize; ++r) *cluster.map_shared_rank(&s_task, r) = t0;
+      }
+      cluster.sync();
+    } else {
+      if (tid == 0) s_task = atomicAdd(P.counter, 1);
+      __syncthreads();
+    }
     const int t = s_task;
-    __syncthreads();
+    if constexpr (CL) cg::this_cluster().sync();
+    else __syncthreads();
     if (t >= P.ntasks) break;
     const TridiagTask task = P.tasks[t];
     const int skip = task.skip;
@@ -303,7 +344,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
 
     // a1: the minor view -- copy the lower triangle of A without row/col `skip`.
     if (task.rot < 0) {
-      for (int r = warp; r < m; r += W) {
+      for (int r = gwarp; r < m; r += GW) {
         const int i = (skip >= 0 && r >= skip) ? r + 1 : r;
         const double* Arow = task.A + (size_t)i * task.lda;
         for (int c = lane; c <= r; c += 32) {
@@ -321,7 +362,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
       auto a_of = [A, lda](int i, int j) {
         return i >= j ? A[(size_t)i * lda + j] : A[(size_t)j * lda + i];
       };
-      for (int r = warp; r < m; r += W) {
+      for (int r = gwarp; r < m; r += GW) {
         const int i = r >= skip ? r + 1 : r;
         for (int c = lane; c <= r; c += 32) {
           const int j = c >= skip ? c + 1 : c;
@@ -338,7 +379,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
         }
       }
     }
-    __syncthreads();
+    block_or_cluster_sync<CL>();
 
     for (int k = 0; k + 2 < m; ++k) {
       const int base = k + 1;
@@ -349,7 +390,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
         double a = S[(size_t)i * ld + k];
         if (upd) a = fma(-vP[i], wPk, fma(-wP[i], vPk, a));
         if (i == k) {
-          dout[k] = a;
+          if (crank == 0) dout[k] = a;
         } else if (i == k + 1) {
           scal[0] = a;       // alpha
           vC[i] = 1.0;
@@ -373,7 +414,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
         if (lane == 0) {
           scal[1] = tau;
           scal[2] = scale;
-          eout[k] = beta;
+          if (crank == 0) eout[k] = beta;
         }
       }
       __syncthreads();
@@ -410,7 +451,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
         // contiguous, balanced range of tiles per warp; each tile leaves its column
         // partial in tpart and its row partial in upart (both indexed by tile)
         const int T = nb * (nb + 1) / 2;
-        const int t0 = tile_start(warp, T, W), t1 = tile_start(warp + 1, T, W);
+        const int t0 = tile_start(gwarp, T, GW), t1 = tile_start(gwarp + 1, T, GW);
         int I = 0;
         while ((I + 1) * (I + 2) / 2 <= t0) ++I;
         int J = t0 - I * (I + 1) / 2;
@@ -432,9 +473,11 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
           if (++J > I) { ++I; J = 0; }
         }
       }
-      __syncthreads();
+      block_or_cluster_sync<CL>();
       // ---- Phase E: p = tau * (row partials + column partials); gamma = tau/2 p.v
-      for (int i = base + tid; i < m; i += NT) {
+      // (cluster variant: each CTA sums every csize-th run of NT elements and writes
+      // them into the w of every CTA of the cluster)
+      for (int i = base + crank * NT + tid; i < m; i += GW * 32) {
         const int r = i - base, I = r >> 5, l = r & 31;
         double p;
         if (SMEM) {
@@ -446,9 +489,15 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
           for (int J = 1; J <= I; ++J) p += up[(size_t)J * 32];
         }
         for (int I2 = I; I2 < nb; ++I2) p += tpart[((size_t)I2 * nbmax + I) * 32 + l];
-        wC[i] = p * tau;
+        if constexpr (CL) {
+          cg::cluster_group cluster = cg::this_cluster();
+          for (int r2 = 0; r2 < csize; ++r2) cluster.map_shared_rank(wC, r2)[i] = p * tau;
+        } else {
+          wC[i] = p * tau;
+        }
       }
-      __syncthreads();
+      if constexpr (CL) cg::this_cluster().sync();
+      else __syncthreads();
       if (warp == 0) {
         const double dot = warp_dot(wC, vC, base, m, lane);
         if (lane == 0) scal[3] = 0.5 * tau * dot;
@@ -463,7 +512,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag
       double* tv = vP; vP = vC; vC = tv;
     }
     // Last 2x2 block (or 1x1): apply the final update and read off d, e.
-    if (tid == 0) {
+    if (tid == 0 && crank == 0) {
       if (m == 1) {
         dout[0] = S[0];
       } else {
@@ -540,6 +589,94 @@ cudaError_t launch_tridiag(bool smem_path, int warps, int grid, const TridiagLau
   return cudaErrorInvalidValue;
 }
 
+// ---- cluster variant: one cluster of C CTAs per matrix (global-slot path)
+
+template <int W>
+std::atomic<uint64_t>& cluster_attr_set() {
+  static std::atomic<uint64_t> done{0};
+  return done;
+}
+
+// Shared-memory limit and permission for clusters above the portable size of 8, once
+// per device (see raise_smem_limit_once for why attributes are set only once).
+template <int W>
+static cudaError_t prepare_cluster_kernel() {
+  const void* kern = (const void*)k_tridiag<false, W, true>;
+  cudaError_t e = raise_smem_limit_once(kern, smem_limit_set<false, W + 100>());
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? 1ull << dev : 0;
+  if (cluster_attr_set<W>().load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) cluster_attr_set<W>().fetch_or(bit, std::memory_order_release);
+  return e;
+}
+
+template <int W>
+static cudaLaunchConfig_t cluster_config(int nclusters, int csize, size_t smem, cudaStream_t s,
+                                         cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nclusters * csize), 1, 1);
+  cfg.blockDim = dim3(W * 32, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <int W>
+static cudaError_t launch_cluster_one(int nclusters, int csize, const TridiagLaunch& L,
+                                      cudaStream_t s) {
+  cudaError_t e = prepare_cluster_kernel<W>();
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg =
+      cluster_config<W>(nclusters, csize, tridiag_smem_bytes(false, L.max_m, W), s, attr);
+  e = cudaLaunchKernelEx(&cfg, k_tridiag<false, W, true>, L);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_cluster(int warps, int nclusters, int csize, const TridiagLaunch& L,
+                                   cudaStream_t s) {
+  switch (warps) {
+    case 8: return launch_cluster_one<8>(nclusters, csize, L, s);
+    case 12: return launch_cluster_one<12>(nclusters, csize, L, s);
+    case 16: return launch_cluster_one<16>(nclusters, csize, L, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Clusters of csize CTAs of the `warps`-warp cluster variant that fit on the device at
+// once for matrices up to max_m (0 if none, or on an error).
+int tridiag_max_active_clusters(int warps, int csize, int max_m) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  cudaLaunchAttribute attr[1];
+#define EEID_CLQ(W_)                                                                            \
+  if (warps == W_) {                                                                             \
+    e = prepare_cluster_kernel<W_>();                                                            \
+    if (e == cudaSuccess) {                                                                      \
+      cudaLaunchConfig_t cfg =                                                                   \
+          cluster_config<W_>(1, csize, tridiag_smem_bytes(false, max_m, W_), nullptr, attr);    \
+      e = cudaOccupancyMaxActiveClusters(&n, k_tridiag<false, W_, true>, &cfg);                  \
+    }                                                                                            \
+  }
+  EEID_CLQ(8) EEID_CLQ(12) EEID_CLQ(16)
+#undef EEID_CLQ
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 // Occupancy query used by the planner to size persistent grids.
 cudaError_t preload_tridiag() {
   cudaError_t e = cudaSuccess;
@@ -548,6 +685,9 @@ cudaError_t preload_tridiag() {
   EEID_PRE(true, 1) EEID_PRE(true, 2) EEID_PRE(true, 4) EEID_PRE(true, 8)
   EEID_PRE(false, 2) EEID_PRE(false, 4) EEID_PRE(false, 8) EEID_PRE(false, 12) EEID_PRE(false, 16)
 #undef EEID_PRE
+  if (e == cudaSuccess) e = prepare_cluster_kernel<8>();
+  if (e == cudaSuccess) e = prepare_cluster_kernel<12>();
+  if (e == cudaSuccess) e = prepare_cluster_kernel<16>();
   return e;
 }
 

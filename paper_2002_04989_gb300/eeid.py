@@ -78,6 +78,8 @@ SIGNATURES = {
                         ctypes.c_int),
     "eeid_components_host": ([_vp, _vp, _i64, _i64, _i64p, _i64, _i64p, _i64, _vp, _vp, _vp],
                              ctypes.c_int),
+    "eeid_components_herm": ([_vp, _vp, _i64, _i64, _i64p, _i64, _i64p, _i64, _vp, _vp, _vp],
+                             ctypes.c_int),
     "eeid_eigenvectors": ([_vp, _vp, _i64, _i64, _i64p, _i64, _vp, _vp, _vp], ctypes.c_int),
     "eeid_components_batched": ([_vp, ctypes.POINTER(EeidProblem), _i64, _vp], ctypes.c_int),
     "eeid_launch_count": ([_vp], ctypes.c_int64),
@@ -90,6 +92,7 @@ SIGNATURES = {
     "eeid_eigvals_noalloc": ([_vp, _i64, _i64, _vp, _vp, _vp], ctypes.c_int),
     "eeid_set_graphs": ([_vp, ctypes.c_int], ctypes.c_int),
     "eeid_set_overlap": ([_vp, ctypes.c_int], ctypes.c_int),
+    "eeid_set_clusters": ([_vp, ctypes.c_int], ctypes.c_int),
     "eeid_server_create": ([ctypes.c_int, ctypes.POINTER(EeidServerOpts), ctypes.POINTER(_vp)],
                            ctypes.c_int),
     "eeid_server_destroy": ([_vp], None),
@@ -162,6 +165,16 @@ def _mat(A):
     if A.dim() != 2 or A.shape[0] != A.shape[1] or A.stride(1) != 1:
         raise ValueError("A must be a square matrix with unit column stride (row-major)")
     return A, int(A.stride(0)) if A.shape[0] > 0 else max(1, A.shape[0])
+
+
+def _cmat(A):
+    """A complex128 CUDA matrix with unit column stride: (A, lda in complex elements)."""
+    import torch
+    if not (isinstance(A, torch.Tensor) and A.is_cuda and A.dtype == torch.complex128):
+        raise TypeError("A must be a complex128 CUDA tensor")
+    if A.dim() != 2 or A.shape[0] != A.shape[1] or A.stride(1) != 1:
+        raise ValueError("A must be a square matrix with unit column stride (row-major)")
+    return A, int(A.stride(0)) if A.shape[0] > 0 else 1
 
 
 def _out(t, numel, like, name, dtype=None):
@@ -280,6 +293,25 @@ class Context:
                                         _stream(stream)))
         return o
 
+    def eeid_components_herm(self, A, rows=None, cols=None, out=None, lam=None, stream=None):
+        """|v_ij|^2 of a complex Hermitian A (complex128 CUDA tensor, lower triangle read)."""
+        import torch
+        A, lda = _cmat(A)
+        n = A.shape[0]
+        rp, nr, k1 = _idx(rows)
+        cp, nc, k2 = _idx(cols)
+        nr = n if rp is None else nr
+        nc = n if cp is None else nc
+        o = (_out(out, nr * nc, A, "out") if out is not None
+             else torch.empty((nr, nc), dtype=torch.float64, device=A.device))
+        if lam is not None:
+            _out(lam, n, A, "lam")
+        _check(self.lib.eeid_components_herm(self.handle, _vp(A.data_ptr()), lda, n, rp, nr, cp,
+                                             nc, _vp(o.data_ptr()),
+                                             _vp(lam.data_ptr()) if lam is not None else None,
+                                             _stream(stream)))
+        return o
+
     def eeid_eigenvectors(self, A, rows=None, out=None, lam=None, stream=None):
         """Signed unit eigenvectors: out[r, j] = v_ij for i = rows[r] (all if None)."""
         import torch
@@ -342,6 +374,9 @@ class Context:
 
     def eeid_set_overlap(self, enable: bool = True) -> int:
         return _check(self.lib.eeid_set_overlap(self.handle, 1 if enable else 0), False)
+
+    def eeid_set_clusters(self, enable: bool = True) -> int:
+        return _check(self.lib.eeid_set_clusters(self.handle, 1 if enable else 0), False)
 
     def launch_count(self) -> int:
         return int(self.lib.eeid_launch_count(self.handle))

@@ -17,6 +17,8 @@ families the build is measured on):
 * ``goe(n, seed)``        A = (G + G^T)/2, G i.i.d. N(0, 1), filled row-major.
 * ``wishart(n, seed)``    A = X^T X / (2n), X 2n x n i.i.d. N(0, 1).
 * ``toeplitz(n, a, b)``   tridiagonal Toeplitz, diagonal a, off-diagonals b.
+* ``goe_herm``, ``planted_herm``  the complex Hermitian counterparts (G = X + iY;
+  Q unitary from a complex QR).
 * ``planted(n, seed, lo, hi, gap)``  A = Q diag(lam) Q^T with Q the orthogonal
   factor of a Householder QR (LAPACK, via numpy) of a seeded Gaussian matrix and
   lam spread on [lo, hi] with every gap >= ``gap`` (n sorted uniforms on
@@ -93,6 +95,32 @@ def planted(n: int, seed: int, lo: float = -1.0, hi: float = 1.0, gap: float = 1
     Q, _ = np.linalg.qr(G)
     lam = planted_spectrum(n, lo, hi, gap, g)
     A = _mirror_lower((Q * lam) @ Q.T)
+    return Planted(A=A, lam=lam, Q=np.ascontiguousarray(Q))
+
+
+def _mirror_lower_herm(A: np.ndarray) -> np.ndarray:
+    L = np.tril(A)
+    H = L + np.tril(L, -1).conj().T
+    H[np.diag_indices_from(H)] = H.diagonal().real
+    return np.ascontiguousarray(H)
+
+
+def goe_herm(n: int, seed: int, g: np.random.Generator | None = None) -> np.ndarray:
+    """Complex Hermitian A = (G + G^H)/2 with G = X + iY, X, Y i.i.d. N(0, 1)."""
+    g = g if g is not None else rng(seed)
+    G = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    return _mirror_lower_herm((G + G.conj().T) / 2)
+
+
+def planted_herm(n: int, seed: int, lo: float = -1.0, hi: float = 1.0, gap: float = 1e-4,
+                 g: np.random.Generator | None = None) -> Planted:
+    """Complex Hermitian A = Q diag(lam) Q^H, Q the unitary factor of a Householder QR
+    (LAPACK, via numpy) of a seeded complex Gaussian matrix; lam as in ``planted``."""
+    g = g if g is not None else rng(seed)
+    G = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    Q, _ = np.linalg.qr(G)
+    lam = planted_spectrum(n, lo, hi, gap, g)
+    A = _mirror_lower_herm((Q * lam) @ Q.conj().T)
     return Planted(A=A, lam=lam, Q=np.ascontiguousarray(Q))
 
 

@@ -1,7 +1,7 @@
 """Host-side planning rules of the CUDA path (csrc/host_plan.h), compiled with the host
 C++ compiler and checked on the CPU: how a group of near-equal Householder reductions is
 split into launches (hybrid rounds, tail overlap), the serving cost bands, and the
-serving loop's pinned staging allocator."""
+serving loop's pinned staging allocator, and the cluster plan of few large reductions."""
 import os
 import shutil
 import subprocess
@@ -27,6 +27,8 @@ int main(int argc, char** argv) {
     for (int i = 0; i < 7; ++i) a[i] = atoi(argv[2 + i]);
     RoundPlan p = plan_rounds(a[0], a[1], a[2], a[3] != 0, a[4], a[5] != 0, a[6]);
     printf("%d %d %d %d\n", p.hybrid ? 1 : 0, p.bulk_grid, p.tail_at, p.tail_grid);
+  } else if (!strcmp(argv[1], "cluster")) {
+    printf("%d\n", cluster_size_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])));
   } else if (!strcmp(argv[1], "band")) {
     printf("%d\n", cost_band(atoll(argv[2]), atoll(argv[3])));
   } else if (!strcmp(argv[1], "pool")) {
@@ -157,3 +159,25 @@ def test_pinned_pool(driver, seed):
     assert takes > 5000
     # everything given back coalesces into the one region it started as
     assert (nfree, off, length) == (1, 0, 1 << 24)
+
+
+def test_cluster_plan(driver):
+    c = lambda nt, sms=152, m=4001: int(driver("cluster", nt, sms, m)[0])
+    # one component of n = 4002 (A and one minor): two clusters of 16 CTAs
+    assert c(2) == 16
+    # the eigenvalues of one large A: one cluster of 16
+    assert c(1) == 16
+    # a few columns: the largest power of two with nt * C <= SMs
+    assert c(5) == 16 and c(10) == 8 and c(19) == 8 and c(20) == 4 and c(38) == 4
+    assert c(39) == 2 and c(76) == 2
+    # more matrices than half the SMs, or small matrices: one CTA per matrix
+    assert c(77) == 0 and c(1025) == 0 and c(2, m=383) == 0
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        nt, sms = int(rng.integers(1, 120)), int(rng.integers(2, 200))
+        k = c(nt, sms)
+        if k:
+            assert k & (k - 1) == 0 and 2 <= k <= 16 and nt * k <= sms
+            assert k == 16 or nt * 2 * k > sms       # the largest such power of two
+        else:
+            assert 2 * nt > sms

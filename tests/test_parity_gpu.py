@@ -535,3 +535,23 @@ def test_hybrid_rounds_bitwise_at_benchmark_size(torch_cuda):
             c.close()
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
     assert np.max(np.abs(res[0][0] - (p.Q * p.Q).T)) <= TOL_VSQ
+
+
+def test_status_is_per_stream(torch_cuda, ctx):
+    """Deferred warnings belong to the stream of the call that raised them: a degenerate
+    matrix on one stream and a small-gap matrix on another, each eeid_sync returns its
+    own stream's warning (calls ordered by an event, as the shared workspace requires)."""
+    from paper_2002_04989_gb300 import eeid
+    torch = torch_cuda
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    deg = torch.from_numpy(np.diag([1.0, 1.0, 2.0, 3.0])).cuda()
+    gap = torch.from_numpy(np.diag([1.0, 1.0 + 1e-7, 2.0, 3.0])).cuda()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        ctx.eeid_components(deg, stream=s1)
+    s2.wait_stream(s1)
+    with torch.cuda.stream(s2):
+        ctx.eeid_components(gap, stream=s2)
+    assert ctx.eeid_sync(s2) == eeid.EEID_WARN_SMALL_GAP
+    assert ctx.eeid_sync(s1) == eeid.EEID_WARN_DEGENERATE
+    assert ctx.eeid_sync(s1) == eeid.EEID_OK and ctx.eeid_sync(s2) == eeid.EEID_OK
