@@ -15,7 +15,7 @@
 #include <vector>
 
 namespace eeid {
-int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m);
+int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m, bool hi);
 cudaError_t launch_tridiag_cluster(int warps, int nclusters, int csize, const TridiagLaunch& L,
                                    cudaStream_t s);
 int tridiag_max_active_clusters(int warps, int csize, int max_m);
@@ -95,9 +95,11 @@ struct eeid_ctx {
   cudaEvent_t stage_ev = nullptr;
   bool stage_used = false;
   int64_t launches = 0;
-  int occ_cache[2][17] = {};  // blocks/SM per (smem path, warps) at the last max_m
-  int occ_m[2][17] = {};
-  struct Rule { int lo, hi; bool smem; int warps; };
+  int occ_cache[3][17] = {};  // blocks/SM per (path, warps) at the last max_m
+  int occ_m[3][17] = {};
+  // path: 0 = working matrix in shared memory, 1 = global slot, 2 = global slot built
+  // for high occupancy
+  struct Rule { int lo, hi; int path; int warps; };
   std::vector<Rule> rules;  // tuning overrides, later ones win
   int rules_version = 0;
   // CUDA graphs of batched calls, keyed by the full description of the batch.
@@ -149,7 +151,10 @@ struct TriCfg {
   bool smem;
   int warps;
   bool herm = false;   // complex Hermitian reduction (its own kernel, global slots)
+  bool hi = false;     // high-occupancy build of the global-slot variant
 };
+inline TriCfg cfg_of(int path, int warps) { return {path == 0, warps, false, path == 2}; }
+inline int path_of(const TriCfg& c) { return c.smem ? 0 : c.hi ? 2 : 1; }
 constexpr int kHermMaxM = 2048;   // largest complex Hermitian matrix (shared-memory vectors)
 constexpr size_t kMaxSmemPerBlock = 232448;  // opt-in shared memory per CTA on sm_103a
 
@@ -162,17 +167,29 @@ TriCfg tri_cfg_default(int m) {
   if (tridiag_smem_bytes(false, m, 12) <= kMaxSmemPerBlock) return {false, 12};
   return {false, 8};
 }
-inline int cfg_key(const TriCfg& c) { return c.herm ? 96 + c.warps : (c.smem ? 0 : 32) + c.warps; }
+inline int cfg_key(const TriCfg& c) {
+  return c.herm ? 96 + c.warps : c.hi ? 64 + c.warps : (c.smem ? 0 : 32) + c.warps;
+}
+
+// Warps per CTA of the cluster variant for m x m matrices: the most that fit.
+int cluster_warps(int m) {
+  for (int w : {16, 12, 8})
+    if (tridiag_smem_bytes(false, m, w) <= kMaxSmemPerBlock) return w;
+  return 0;
+}
 
 TriCfg herm_cfg(int m) {
   return {false, tridiag_herm_smem_bytes(m, 8) <= kMaxSmemPerBlock ? 8 : 4, true};
 }
 
-bool cfg_supported(bool smem, int warps, int m) {
+bool cfg_supported(int path, int warps, int m) {
   bool ok;
-  if (smem) ok = (warps == 1 || warps == 2 || warps == 4 || warps == 8) && m <= kTridiagSmemMaxM;
-  else ok = (warps == 2 || warps == 4 || warps == 8 || warps == 12 || warps == 16) && m <= kTridiagMaxM;
-  return ok && tridiag_smem_bytes(smem, m, warps) <= kMaxSmemPerBlock;
+  if (path == 0) ok = (warps == 1 || warps == 2 || warps == 4 || warps == 8) && m <= kTridiagSmemMaxM;
+  else if (path == 1)
+    ok = (warps == 2 || warps == 4 || warps == 8 || warps == 12 || warps == 16) && m <= kTridiagMaxM;
+  else if (path == 2) ok = (warps == 4 || warps == 8) && m <= kTridiagMaxM;
+  else ok = false;
+  return ok && tridiag_smem_bytes(path == 0, m, warps) <= kMaxSmemPerBlock;
 }
 
 struct Problem {
@@ -315,8 +332,8 @@ int status_slot(eeid_ctx* ctx, cudaStream_t s, bool assign) {
 
 TriCfg tri_cfg(const eeid_ctx* ctx, int m) {
   for (auto it = ctx->rules.rbegin(); it != ctx->rules.rend(); ++it)
-    if (m >= it->lo && m <= it->hi && cfg_supported(it->smem, it->warps, m))
-      return {it->smem, it->warps};
+    if (m >= it->lo && m <= it->hi && cfg_supported(it->path, it->warps, m))
+      return cfg_of(it->path, it->warps);
   return tri_cfg_default(m);
 }
 
@@ -330,10 +347,10 @@ bool rule_covers(const eeid_ctx* ctx, int m) {
 
 int blocks_per_sm(eeid_ctx* ctx, const TriCfg& c, int max_m) {
   if (c.herm) return std::max(1, tridiag_herm_blocks_per_sm(c.warps, max_m));
-  int& cache = ctx->occ_cache[c.smem ? 0 : 1][c.warps];
-  int& cm = ctx->occ_m[c.smem ? 0 : 1][c.warps];
+  int& cache = ctx->occ_cache[path_of(c)][c.warps];
+  int& cm = ctx->occ_m[path_of(c)][c.warps];
   if (cache == 0 || cm != max_m) {
-    cache = std::max(1, tridiag_blocks_per_sm(c.smem, c.warps, max_m));
+    cache = std::max(1, tridiag_blocks_per_sm(c.smem, c.warps, max_m, c.hi));
     cm = max_m;
   }
   return cache;
@@ -431,6 +448,23 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     const int bps = blocks_per_sm(ctx, g.cfg, g.max_m);
     const int sms_used = std::max(1, ctx->sms - ctx->sm_reserve);
     g.grid = (int)std::min<int64_t>((int64_t)g.idx.size(), (int64_t)sms_used * bps);
+    // Round launches (serving) of a large group: rounds of two 8-warp CTAs per SM when
+    // they finish the group sooner than rounds of one wide CTA per SM (a pair-round takes
+    // kRound8x2Per16 single rounds for twice the matrices), as in the plain path's
+    // hybrid rounds.  Bitwise the same results.
+    if (ctx->round_launches && ctx->overlap_enabled && !g.cfg.smem && !g.cfg.herm &&
+        g.cfg.warps >= 12 && bps == 1 && g.grid == sms_used && !rule_covers(ctx, g.max_m) &&
+        cfg_supported(1, 8, g.max_m)) {
+      const TriCfg c8{false, 8};
+      const int b8 = blocks_per_sm(ctx, c8, g.max_m);
+      const int nt = (int)g.idx.size(), g8 = sms_used * b8;
+      const double t_pairs = (double)((nt + g8 - 1) / g8) * kRound8x2Per16;
+      const double t_single = (double)((nt + g.grid - 1) / g.grid);
+      if (b8 >= 2 && nt > g.grid && t_pairs < t_single) {
+        g.cfg = c8;
+        g.grid = g8;
+      }
+    }
     g.slot = g.cfg.herm ? tridiag_herm_slot_doubles(g.max_m)
              : g.cfg.smem ? 0 : tridiag_global_slot_doubles(g.max_m);
     g.work_off = 0;  // assigned after the rest of the layout (see below)
@@ -447,9 +481,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     GroupPlan& g = gplans[0];
     const int nt = (int)g.idx.size();
     int c = cluster_size_for(nt, std::max(1, ctx->sms - ctx->sm_reserve), g.max_m);
-    int w = 0;
-    for (int cand : {16, 12, 8})
-      if (!w && tridiag_smem_bytes(false, g.max_m, cand) <= kMaxSmemPerBlock) w = cand;
+    const int w = cluster_warps(g.max_m);
     while (c >= 2 && w && tridiag_max_active_clusters(w, c, g.max_m) < nt) c /= 2;
     if (c >= 2 && w) {
       g.csize = c;
@@ -471,6 +503,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   // bitwise the same (d, e), so the plan never shows in the results.
   int tail_at = 0, tail_grid = 0, tail_grid_of = 0;
   TriCfg tail_cfg{false, 0};
+  int tail_csize = 0;   // the tail launch's cluster size (0: one CTA per matrix)
   size_t counter2_off = 0;
   std::vector<char> in_tail(tri.size(), 0);
   if (ctx->overlap_enabled && !ctx->round_launches && gplans.size() == 1 && mode != MODE_EIGVALS &&
@@ -490,15 +523,42 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
       if (tri[g.idx[q]].col < 0) last_a = q;
     const TriCfg c8{false, 8};
     const bool wide = !g.cfg.smem && g.cfg.warps >= 12;
-    const int blocks8 = (wide && !rule_covers(ctx, g.max_m) && cfg_supported(false, 8, g.max_m))
+    const int blocks8 = (wide && !rule_covers(ctx, g.max_m) && cfg_supported(1, 8, g.max_m))
                             ? blocks_per_sm(ctx, c8, g.max_m) : 0;
     const RoundPlan rp = plan_rounds(nt, g.grid, ctx->sms, wide, blocks8, uniform, last_a);
     tail_cfg = g.cfg;   // the tail runs the group's default variant
-    if (rp.hybrid) {
-      g.cfg = c8;
-      g.grid = rp.bulk_grid;
+    // Cluster rounds instead, when the estimate says they keep the SMs busier than the
+    // one-CTA plan (see plan_cluster_rounds).  Same bitwise results either way.
+    ClusterRounds cr;
+    if (ctx->clusters_enabled && uniform && !g.cfg.smem && !rule_covers(ctx, g.max_m) &&
+        g.grid == ctx->sms && 2 * nt > ctx->sms) {
+      const int w = g.cfg.warps;
+      int active[4];
+      for (int k = 0; k < 4; ++k) active[k] = tridiag_max_active_clusters(w, 2 << k, g.max_m);
+      double t_single;
+      if (rp.hybrid) {
+        const int bulk = rp.tail_at > 0 ? rp.tail_at : nt;
+        t_single = (double)(bulk / rp.bulk_grid) * kRound8x2Per16 + (rp.tail_at > 0 ? 1.0 : 0.0);
+      } else {
+        t_single = (double)((nt + g.grid - 1) / g.grid);
+      }
+      cr = plan_cluster_rounds(nt, ctx->sms, g.max_m, active, t_single);
+      if (cr.c1 && last_a >= cr.bulk) cr = ClusterRounds();
     }
-    if (rp.tail_at > 0) split_at(rp.tail_at, rp.tail_grid);
+    if (cr.c1) {
+      g.csize = cr.c1;
+      g.grid = cr.per_round;   // clusters (= slots)
+      if (cr.bulk < nt) {
+        split_at(cr.bulk, nt - cr.bulk);
+        tail_csize = cr.c2;
+      }
+    } else {
+      if (rp.hybrid) {
+        g.cfg = c8;
+        g.grid = rp.bulk_grid;
+      }
+      if (rp.tail_at > 0) split_at(rp.tail_at, rp.tail_grid);
+    }
   }
   // bisection tasks: A's first (their eigenvalues seed the minors' brackets); with the
   // tail overlap the minors of the tail are bisected in a second launch
@@ -506,13 +566,22 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   for (size_t t = 0; t < tri.size(); ++t)
     (tri[t].col < 0 ? bis_a : in_tail[t] ? bis_m2 : bis_m).push_back((int)t);
   const size_t bt_off = meta.take(sizeof(BisectTask) * tri.size());
+  // Bisection blocks, largest tasks first.  Runs of consecutive tasks (the minors of one
+  // matrix) of one small size m share a block, kBisectThreads / m of them at a time.
   auto items_of = [&](const std::vector<int>& ts, std::vector<BisectItem>& items, int& mm) {
     std::vector<int> order = ts;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tri[a].m > tri[b].m; });
     mm = 1;
-    for (int t : order) {
-      mm = std::max(mm, tri[t].m);
-      for (int k0 = 0; k0 < tri[t].m; k0 += kBisectThreads) items.push_back({t, k0});
+    for (int t : order) mm = std::max(mm, tri[t].m);
+    std::vector<BisectBlock> blocks;
+    plan_bisect_blocks(order, [&](int t) { return tri[t].m; }, kBisectThreads, kBisectMaxPack,
+                       blocks);
+    for (const BisectBlock& b : blocks) {
+      BisectItem it;
+      it.task = b.task;
+      it.k0 = b.k0;
+      it.ntask = b.ntask;
+      items.push_back(it);
     }
   };
   std::vector<BisectItem> items_a, items_m, items_m2;
@@ -528,7 +597,8 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   const size_t bim2_off = bim_off + sizeof(BisectItem) * items_m.size();
   // identity
   std::vector<IdentityItem> iitems;
-  size_t dt_off = 0, ip_off = 0, ii_off = 0;
+  std::vector<DenomItem> ditems;
+  size_t dt_off = 0, ip_off = 0, ii_off = 0, di_off = 0;
   std::vector<size_t> rows_off(probs.size(), 0);
   if (mode == MODE_COMPONENTS) {
     for (size_t p = 0; p < probs.size(); ++p)
@@ -536,6 +606,11 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
         rows_off[p] = meta.take(sizeof(int) * std::max<size_t>(probs[p].rows.size(), 1));
     dt_off = meta.take(sizeof(DenomTask) * probs.size());
     ip_off = meta.take(sizeof(IdentityProblem) * probs.size());
+    for (size_t p = 0; p < probs.size(); ++p)
+      if (probs[p].n >= 1)
+        for (int r0 = 0; r0 < (int)probs[p].rows.size(); r0 += kDenomThreads)
+          ditems.push_back({(int)p, r0});
+    di_off = meta.take(sizeof(DenomItem) * std::max<size_t>(ditems.size(), 1));
     for (size_t p = 0; p < probs.size(); ++p) {
       const Problem& P = probs[p];
       if (P.n < 1) continue;
@@ -640,13 +715,15 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     for (size_t p = 0; p < probs.size(); ++p) {
       const Problem& P = probs[p];
       if (P.n < 1) continue;
-      dt[p] = {lam_ptr((int)p), P.n, D(dm_off[p]), (int*)(wd + de_off[p])};
+      dt[p] = {lam_ptr((int)p), P.n, D(dm_off[p]), (int*)(wd + de_off[p]),
+               (const int*)(ws + rows_off[p]), (int)P.rows.size()};
       memcpy(img + rows_off[p], P.rows.data(), sizeof(int) * P.rows.size());
       ip[p] = {lam_ptr((int)p), D(dm_off[p]), (const int*)(wd + de_off[p]),
                P.n >= 2 ? mu_ptr((int)p) : nullptr, (const int*)(ws + rows_off[p]), P.n,
                (int)P.rows.size(), (int)P.cols.size(), P.out};
     }
     if (!iitems.empty()) memcpy(img + ii_off, iitems.data(), sizeof(IdentityItem) * iitems.size());
+    if (!ditems.empty()) memcpy(img + di_off, ditems.data(), sizeof(DenomItem) * ditems.size());
   }
   auto enqueue_launches = [&]() -> eeid_status {
   // ---- launches (optionally bracketed by per-phase events)
@@ -670,11 +747,26 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     L.status = status_word;
     auto launch_group = [&](int grid, const TridiagLaunch& LL, cudaStream_t on) {
       return g.cfg.herm ? launch_tridiag_herm(g.cfg.warps, grid, LL, on)
-                        : launch_tridiag(g.cfg.smem, g.cfg.warps, grid, LL, on);
+                        : launch_tridiag(g.cfg.smem, g.cfg.warps, grid, LL, on, g.cfg.hi);
     };
     if (g.nchunks > 1) {
-      // round launches: chunk c takes tasks [c*chunk, ...) with its own counter
-      const int total = L.ntasks, chunk = (total + g.nchunks - 1) / g.nchunks;
+      // round launches: chunk c takes tasks [c*chunk, ...) with its own counter.  When the
+      // last round would be short (at most half the SMs' worth of matrices), the whole
+      // rounds are launched full and that remainder runs as one launch of clusters.
+      const int total = L.ntasks;
+      int chunk = (total + g.nchunks - 1) / g.nchunks, last_c = 0, last_w = 0;
+      if (ctx->clusters_enabled && !g.cfg.smem && !g.cfg.herm && !rule_covers(ctx, g.max_m)) {
+        const int rem = total % g.grid;
+        const int sms_used = std::max(1, ctx->sms - ctx->sm_reserve);
+        const int w = cluster_warps(g.max_m);
+        int c = rem > 0 && w ? cluster_size_for(rem, sms_used, g.max_m) : 0;
+        while (c >= 2 && tridiag_max_active_clusters(w, c, g.max_m) < rem) c /= 2;
+        if (c >= 2) {
+          chunk = g.grid;
+          last_c = c;
+          last_w = w;
+        }
+      }
       const TridiagTask* t0 = L.tasks;
       for (int c = 0; c < g.nchunks; ++c) {
         const int a = c * chunk, b = std::min(total, a + chunk);
@@ -682,7 +774,11 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
         L.tasks = t0 + a;
         L.ntasks = b - a;
         L.counter = (int*)(ws + g.counter_off) + c;
-        EEID_CK(launch_group(std::min(g.grid, b - a), L, stream), "tridiag launch");
+        if (last_c && b - a < chunk)
+          EEID_CK(launch_tridiag_cluster(last_w, b - a, last_c, L, stream),
+                  "tridiag cluster launch");
+        else
+          EEID_CK(launch_group(std::min(g.grid, b - a), L, stream), "tridiag launch");
         ctx->launches++;
       }
       continue;
@@ -690,10 +786,9 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     if (g.csize) {
       EEID_CK(launch_tridiag_cluster(g.cfg.warps, g.grid, g.csize, L, stream),
               "tridiag cluster launch");
-      ctx->launches++;
-      continue;
+    } else {
+      EEID_CK(launch_group(g.grid, L, stream), "tridiag launch");
     }
-    EEID_CK(launch_group(g.grid, L, stream), "tridiag launch");
     ctx->launches++;
     if (tail_at > 0) {
       // the tail: same slots (the first launch is done with them), its own counter
@@ -702,8 +797,12 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
       L.tasks += tail_at;
       L.ntasks = (int)g.idx.size() - tail_at;
       L.counter = (int*)(ws + counter2_off);
-      EEID_CK(launch_tridiag(tail_cfg.smem, tail_cfg.warps, tail_grid, L, ctx->aux_stream),
-              "tridiag tail launch");
+      if (tail_csize)
+        EEID_CK(launch_tridiag_cluster(tail_cfg.warps, tail_grid, tail_csize, L, ctx->aux_stream),
+                "tridiag tail cluster launch");
+      else
+        EEID_CK(launch_tridiag(tail_cfg.smem, tail_cfg.warps, tail_grid, L, ctx->aux_stream),
+                "tridiag tail launch");
       ctx->launches++;
     }
   }
@@ -723,7 +822,8 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   }
   if (mode == MODE_COMPONENTS) {
     EEID_CK(mark(EEID_PHASE_DENOMINATORS, 0, stream), "event");
-    EEID_CK(launch_denominators((const DenomTask*)(ws + dt_off), (int)probs.size(), max_n,
+    EEID_CK(launch_denominators((const DenomTask*)(ws + dt_off), (const DenomItem*)(ws + di_off),
+                                (int)ditems.size(), max_n,
                                 status_word, stream), "denominators launch");
     ctx->launches++;
     EEID_CK(mark(EEID_PHASE_DENOMINATORS, 1, stream), "event");
@@ -864,12 +964,12 @@ int64_t eeid_vector_refs(const eeid_ctx* ctx) { return ctx ? ctx->vec_refs : 0; 
 eeid_status eeid_tune_tridiag(eeid_ctx* ctx, int m_lo, int m_hi, int path, int warps) {
   eeid_status st = check_ctx(ctx);
   if (st != EEID_OK) return st;
-  if (m_lo < 1 || m_hi < m_lo || (path != 0 && path != 1))
+  if (m_lo < 1 || m_hi < m_lo || path < 0 || path > 2)
     return fail(EEID_ERR_INVALID, "bad tuning rule");
-  if (!cfg_supported(path == 0, warps, m_hi))
+  if (!cfg_supported(path, warps, m_hi))
     return fail(EEID_ERR_INVALID, "unsupported variant (path %d, %d warps) for m <= %d", path, warps,
                 m_hi);
-  ctx->rules.push_back({m_lo, m_hi, path == 0, warps});
+  ctx->rules.push_back({m_lo, m_hi, path, warps});
   ctx->rules_version++;
   return EEID_OK;
 }
@@ -882,7 +982,7 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
   cudaDeviceProp prop;
   EEID_CK(cudaGetDeviceProperties(&prop, ctx->device), "cudaGetDeviceProperties");
   char header[384];
-  snprintf(header, sizeof header, "eeid-tune v1 sms=%d name=%s", prop.multiProcessorCount, prop.name);
+  snprintf(header, sizeof header, "eeid-tune v2 sms=%d name=%s", prop.multiProcessorCount, prop.name);
   const int mmax = std::min(max_m, 1024);
   std::vector<eeid_ctx::Rule> chosen;
   // ---- cached table
@@ -897,8 +997,8 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
       }
       int lo, hi, path, w;
       while (ok && fscanf(f, "%d %d %d %d", &lo, &hi, &path, &w) == 4) {
-        if (!cfg_supported(path == 0, w, hi) || lo < 1 || hi < lo) { ok = false; break; }
-        chosen.push_back({lo, hi, path == 0, w});
+        if (!cfg_supported(path, w, hi) || lo < 1 || hi < lo) { ok = false; break; }
+        chosen.push_back({lo, hi, path, w});
       }
       fclose(f);
       if (ok && !chosen.empty() && chosen.back().hi >= mmax) {
@@ -932,10 +1032,10 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
                                         std::min<double>(64.0 * ctx->sms, 3e10 / flops_task));
     struct Cand { TriCfg c; int grid; size_t slot; };
     std::vector<Cand> cands;
-    for (int path = 0; path < 2; ++path)
+    for (int path = 0; path < 3; ++path)
       for (int w : {1, 2, 4, 8, 16}) {
-        if (!cfg_supported(path == 0, w, m)) continue;
-        TriCfg c{path == 0, w};
+        if (!cfg_supported(path, w, m)) continue;
+        TriCfg c = cfg_of(path, w);
         const int grid = (int)std::min<int64_t>(T, (int64_t)ctx->sms * blocks_per_sm(ctx, c, m));
         cands.push_back({c, grid, c.smem ? 0 : tridiag_global_slot_doubles(m)});
       }
@@ -976,7 +1076,7 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
       for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
         ce = cudaMemsetAsync(ws + c_off, 0, sizeof(int), s);
         if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
-        if (ce == cudaSuccess) ce = launch_tridiag(c.c.smem, c.c.warps, c.grid, L, s);
+        if (ce == cudaSuccess) ce = launch_tridiag(c.c.smem, c.c.warps, c.grid, L, s, c.c.hi);
         if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
         if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
         if (ce == cudaSuccess) ce = cudaEventElapsedTime(&msr, e0, e1);
@@ -984,7 +1084,7 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
       if (ce != cudaSuccess) { cleanup(); return cuda_fail(ce, "tune run"); }
       if (msr < best_ms) { best_ms = msr; best = c.c; }
     }
-    chosen.push_back({prev + 1, m, best.smem, best.warps});
+    chosen.push_back({prev + 1, m, path_of(best), best.warps});
     prev = m;
   }
   cleanup();
@@ -994,7 +1094,7 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
     FILE* f = fopen(cache_path, "w");
     if (f) {
       fprintf(f, "%s\n", header);
-      for (auto& r : chosen) fprintf(f, "%d %d %d %d\n", r.lo, r.hi, r.smem ? 0 : 1, r.warps);
+      for (auto& r : chosen) fprintf(f, "%d %d %d %d\n", r.lo, r.hi, r.path, r.warps);
       fclose(f);
     }
   }

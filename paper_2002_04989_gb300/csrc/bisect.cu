@@ -185,65 +185,108 @@ __device__ __forceinline__ int sturm_count_df(const float4* __restrict__ q, int 
 __global__ void __launch_bounds__(kBisectThreads)
 k_bisect(const BisectTask* __restrict__ tasks, const BisectItem* __restrict__ items,
          unsigned* status) {
-  extern __shared__ __align__(16) double2 de[];
+  extern __shared__ __align__(16) double2 de_all[];
   __shared__ double red[3][kBisectThreads / 32];
+  __shared__ double s_g[3][kBisectMaxPack];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const BisectItem it = items[blockIdx.x];
-  const BisectTask T = tasks[it.task];
-  const int m = T.m;
+  const int npack = it.ntask;          // > 1: npack consecutive tasks of one size m
+  const int m = tasks[it.task].m;
+  // this lane's task (local index lt) and eigenvalue index k
+  const int lt = npack > 1 ? tid / m : 0;
+  const bool in_task = lt < npack;
+  const BisectTask T = tasks[it.task + (in_task ? lt : 0)];
+  const int k = npack > 1 ? tid - lt * m : it.k0 + tid;
   if (m == 1) {  // a 1x1 tridiagonal is its own eigenvalue
-    if (it.k0 + tid == 0) T.eig[0] = T.d[0];
+    if (in_task && k == 0) T.eig[0] = T.d[0];
     return;
   }
 
-  // Gershgorin bounds and the spectral scale, from the unscaled entries.
-  double gl = 1e308, gu = -1e308, tn = 0.0;
-  for (int i = tid; i < m; i += blockDim.x) {
-    const double d = T.d[i];
-    const double el = (i > 0) ? fabs(T.e[i - 1]) : 0.0;
-    const double er = (i + 1 < m) ? fabs(T.e[i]) : 0.0;
-    const double r = el + er;
-    gl = fmin(gl, d - r);
-    gu = fmax(gu, d + r);
-    tn = fmax(tn, fabs(d) + r);
-  }
+  // Gershgorin bounds and the spectral scale of each task, from the unscaled entries:
+  // one task per block reduced by the whole block, packed tasks one per warp at a time.
+  if (npack == 1) {
+    double gl = 1e308, gu = -1e308, tn = 0.0;
+    for (int i = tid; i < m; i += blockDim.x) {
+      const double d = T.d[i];
+      const double el = (i > 0) ? fabs(T.e[i - 1]) : 0.0;
+      const double er = (i + 1 < m) ? fabs(T.e[i]) : 0.0;
+      const double r = el + er;
+      gl = fmin(gl, d - r);
+      gu = fmax(gu, d + r);
+      tn = fmax(tn, fabs(d) + r);
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
-    gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
-    tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+      gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+      tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    }
+    if (lane == 0) { red[0][warp] = gl; red[1][warp] = gu; red[2][warp] = tn; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        gl = fmin(gl, red[0][w]);
+        gu = fmax(gu, red[1][w]);
+        tn = fmax(tn, red[2][w]);
+      }
+      s_g[0][0] = gl; s_g[1][0] = gu; s_g[2][0] = tn;
+    }
+  } else {
+    for (int q = warp; q < npack; q += (int)(blockDim.x >> 5)) {
+      const BisectTask Q = tasks[it.task + q];
+      double gl = 1e308, gu = -1e308, tn = 0.0;
+      for (int i = lane; i < m; i += 32) {
+        const double d = Q.d[i];
+        const double el = (i > 0) ? fabs(Q.e[i - 1]) : 0.0;
+        const double er = (i + 1 < m) ? fabs(Q.e[i]) : 0.0;
+        const double r = el + er;
+        gl = fmin(gl, d - r);
+        gu = fmax(gu, d + r);
+        tn = fmax(tn, fabs(d) + r);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+        gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+        tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+      }
+      if (lane == 0) { s_g[0][q] = gl; s_g[1][q] = gu; s_g[2][q] = tn; }
+    }
   }
-  if (lane == 0) { red[0][warp] = gl; red[1][warp] = gu; red[2][warp] = tn; }
   __syncthreads();
-  gl = red[0][0]; gu = red[1][0]; tn = red[2][0];
-  for (int w = 1; w < kBisectThreads / 32; ++w) {
-    gl = fmin(gl, red[0][w]);
-    gu = fmax(gu, red[1][w]);
-    tn = fmax(tn, red[2][w]);
+  // every task's table scaled by an exact power of two to a Gershgorin bound in [0.5, 1);
+  // the tables of packed tasks lie one after the other
+  const int rows = npack * m;
+  float4* dq_all = (float4*)(de_all + (rows > m ? rows : m));   // double-float copies
+  for (int i = tid; i < rows; i += blockDim.x) {
+    const int q = i / m, r = i - q * m;
+    const BisectTask Q = npack > 1 ? tasks[it.task + q] : T;
+    const double tq = s_g[2][q];
+    int exq = 0;
+    if (tq != 0.0) frexp(tq, &exq);
+    const double scq = ldexp(1.0, -exq);
+    const double d = Q.d[r] * scq;
+    const double e = (r > 0) ? Q.e[r - 1] * scq : 0.0;
+    const double e2 = e * e;
+    de_all[i] = make_double2(d, e2);
+    const dflt dd = df_of(d), ee = df_of(e2);
+    dq_all[i] = make_float4(dd.h, dd.l, ee.h, ee.l);
   }
-  const int k = it.k0 + tid;
-  if (tn == 0.0) {  // zero matrix: every eigenvalue is 0
-    if (k < m) T.eig[k] = 0.0;
-    return;
-  }
-  int ex;
-  frexp(tn, &ex);                   // tn * 2^-ex in [0.5, 1)
+  __syncthreads();
+  const double2* de = de_all + lt * m;
+  const float4* dq = dq_all + lt * m;
+  const double gl = s_g[0][in_task ? lt : 0], gu = s_g[1][in_task ? lt : 0];
+  const double tn = s_g[2][in_task ? lt : 0];
+  // a zero matrix has every eigenvalue 0 (its lanes stay in the warp, inactive)
+  const bool zero = tn == 0.0;
+  int ex = 0;
+  if (!zero) frexp(tn, &ex);        // tn * 2^-ex in [0.5, 1)
   const double sc = ldexp(1.0, -ex);
   const double isc = ldexp(1.0, ex);
-  float4* dq = (float4*)(de + m);   // double-float copy of the table
-  for (int i = tid; i < m; i += blockDim.x) {
-    const double d = T.d[i] * sc;
-    const double e = (i > 0) ? T.e[i - 1] * sc : 0.0;
-    const double e2 = e * e;
-    de[i] = make_double2(d, e2);
-    const dflt dd = df_of(d), ee = df_of(e2);
-    dq[i] = make_float4(dd.h, dd.l, ee.h, ee.l);
-  }
-  __syncthreads();
 
   // Scaled Gershgorin bracket, widened by a few ulps of the scale.
   const double glo = gl * sc - 0x1p-45, ghi = gu * sc + 0x1p-45;
-  bool active = k < m;
+  bool active = in_task && k < m && !zero;
   double lo = glo, hi = ghi;
   if (active && T.parent != nullptr) {
     lo = T.parent[k] * sc - 0x1p-40;
@@ -318,7 +361,7 @@ k_bisect(const BisectTask* __restrict__ tasks, const BisectItem* __restrict__ it
       active = (hi - lo > tol) && (++iter < kMaxIter);
     }
   }
-  if (k < m) T.eig[k] = 0.5 * (lo + hi) * isc;
+  if (in_task && k < m) T.eig[k] = zero ? 0.0 : 0.5 * (lo + hi) * isc;
 }
 
 }  // namespace
@@ -330,7 +373,9 @@ cudaError_t preload_bisect() { return raise_smem_limit_once((const void*)k_bisec
 cudaError_t launch_bisect(const BisectTask* tasks, const BisectItem* items, int nitems, int max_m,
                           unsigned* status, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  const size_t smem = (size_t)max_m * (sizeof(double2) + sizeof(float4));
+  // room for one task of max_m rows or for packed tasks of up to kBisectThreads rows
+  const size_t rows = (size_t)(max_m > kBisectThreads ? max_m : kBisectThreads);
+  const size_t smem = rows * (sizeof(double2) + sizeof(float4));
   cudaError_t e = raise_smem_limit_once((const void*)k_bisect, g_bisect_limit_set);
   if (e != cudaSuccess) return e;
   k_bisect<<<nitems, kBisectThreads, smem, s>>>(tasks, items, status);

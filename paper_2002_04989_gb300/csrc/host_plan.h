@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <iterator>
 #include <map>
+#include <vector>
 
 namespace eeid {
 
@@ -83,6 +84,86 @@ inline int cluster_size_for(int nt, int sms, int max_m, int min_m = kClusterMinM
   int c = 1;
   while (2 * c <= kClusterMaxCtas && nt * 2 * c <= sms) c *= 2;
   return c >= 2 ? c : 0;
+}
+
+// Efficiency of a reduction split over a cluster of c CTAs, relative to one CTA, for an
+// m x m matrix.  The phases outside the fused pass (column update, reflector, the sums of
+// the partials, w) run redundantly in every CTA of a cluster and do not shrink with c;
+// they cost about sigma(m) = 40.8/m of a one-CTA step (measured: clusters of 16 at
+// m = 4001 ran at 81% of the per-SM FP64 peak against 94% for one CTA per matrix, so
+// 1/(1 + 16 sigma) = 0.86).  e(c) = 1 / (1 + c sigma(m)).
+constexpr double kClusterSerialPerM = 40.8;
+inline double cluster_efficiency(int c, int m) {
+  return 1.0 / (1.0 + (double)c * kClusterSerialPerM / (double)(m > 0 ? m : 1));
+}
+
+// Cluster rounds for a large uniform group (nt near-equal reductions of size m, more
+// than half the SMs, too many for the one-round cluster plan): whole rounds with
+// clusters of c1 CTAs (bulk tasks), then one launch of the remaining nt - bulk tasks with
+// clusters of c2, so that a partial last round of one CTA per matrix does not leave SMs
+// idle.  active[k] = clusters of 2^(k+1) CTAs the device holds at once (k = 0..3).
+// t_single: the time of the one-CTA plan in units of one one-CTA reduction (the caller
+// takes it from plan_rounds).  Returns c1 = 0 unless the estimate beats t_single by 5%.
+struct ClusterRounds {
+  int c1 = 0;      // cluster size of the whole rounds
+  int per_round = 0;
+  int bulk = 0;    // tasks in the whole rounds
+  int c2 = 0;      // cluster size of the last launch (0: none)
+  double t = 0;    // estimated time, units of one one-CTA reduction
+};
+inline ClusterRounds plan_cluster_rounds(int nt, int sms, int m, const int active[4],
+                                         double t_single, int min_m = kClusterMinM) {
+  ClusterRounds best;
+  if (nt < 1 || m < min_m) return best;
+  for (int k1 = 0; k1 < 2; ++k1) {           // c1 = 2 or 4
+    const int c1 = 2 << k1;
+    const int K = active[k1];
+    if (K < 1) continue;
+    const int rounds = nt / K, rem = nt - rounds * K;
+    double t = rounds / (c1 * cluster_efficiency(c1, m));
+    int c2 = 0;
+    if (rem > 0) {
+      for (int k2 = 3; k2 >= 0 && !c2; --k2) {
+        const int c = 2 << k2;
+        if (rem * c <= sms && active[k2] >= rem) c2 = c;
+      }
+      t += c2 ? 1.0 / (c2 * cluster_efficiency(c2, m)) : 1.0;
+    }
+    if (rounds > 0 && (best.c1 == 0 || t < best.t)) {
+      best.c1 = c1;
+      best.per_round = K;
+      best.bulk = rounds * K;
+      best.c2 = c2;
+      best.t = t;
+    }
+  }
+  if (best.c1 && !(best.t < 0.95 * t_single)) best = ClusterRounds();
+  return best;
+}
+
+// Bisection blocks for a list of tasks (order: task indices, largest first; m_of(t): the
+// size of task t).  A task larger than half a block gets blocks of `threads` eigenvalues
+// each ({t, k0, 1}); runs of consecutive task indices of one size m >= 4 (the minors of
+// one matrix) share a block, up to min(threads / m, max_pack) of them ({t, 0, run}).
+struct BisectBlock {
+  int task, k0, ntask;
+};
+template <class MOf>
+inline void plan_bisect_blocks(const std::vector<int>& order, MOf m_of, int threads, int max_pack,
+                               std::vector<BisectBlock>& out) {
+  for (size_t q = 0; q < order.size();) {
+    const int t = order[q], m = m_of(t);
+    const int cap = (m >= 4 && 2 * m <= threads) ? std::min(threads / m, max_pack) : 1;
+    int run = 1;
+    while (run < cap && q + run < order.size() && order[q + run] == t + run && m_of(t + run) == m)
+      ++run;
+    if (run > 1) {
+      out.push_back({t, 0, run});
+    } else {
+      for (int k0 = 0; k0 < m; k0 += threads) out.push_back({t, k0, 1});
+    }
+    q += (size_t)run;
+  }
 }
 
 // Serving: cost band of a request, from n^3 (columns + 1), which is proportional to its

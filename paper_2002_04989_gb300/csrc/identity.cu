@@ -19,7 +19,8 @@
 // factor is ~0; it is clamped to 0 (the component is then 0).  D_i == 0 (two equal
 // eigenvalues of A) makes Eq. 1 0/0: the component is NaN and a status bit is set.
 //
-// D_i is shared by every j, so it is computed once per problem (k_denominators);
+// D_i is shared by every j, so it is computed once per requested row (k_denominators,
+// one thread per row, the rows of large problems spread over several blocks);
 // k_identity stages mu^(j) in shared memory and gives each thread one (i, j).
 #include "internal.cuh"
 
@@ -57,14 +58,19 @@ __device__ __forceinline__ double clamp_nonneg(double x) {
   return (__double2hiint(x) < 0) ? 0.0 : x;
 }
 
-__global__ void k_denominators(const DenomTask* __restrict__ tasks, unsigned* status) {
+__global__ void __launch_bounds__(kDenomThreads)
+k_denominators(const DenomTask* __restrict__ tasks, const DenomItem* __restrict__ items,
+               unsigned* status) {
   extern __shared__ double lam[];
-  const DenomTask T = tasks[blockIdx.x];
+  const DenomItem it = items[blockIdx.x];
+  const DenomTask T = tasks[it.task];
   const int n = T.n;
   for (int k = threadIdx.x; k < n; k += blockDim.x) lam[k] = T.lam[k];
   __syncthreads();
   bool degenerate = false;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  const int r = it.r0 + threadIdx.x;
+  if (r < T.nrows) {
+    const int i = T.rows[r];
     const double li = lam[i];
     double x = 1.0;
     int ex = 0;
@@ -78,8 +84,9 @@ __global__ void k_denominators(const DenomTask* __restrict__ tasks, unsigned* st
     T.dm[i] = mnt;
     T.de[i] = ex + e2;
   }
-  if (degenerate) atomicOr(status, (unsigned)ST_DEGENERATE);
-  if (threadIdx.x == 0 && n >= 2) {
+  if (__any_sync(0xffffffffu, degenerate) && (threadIdx.x & 31) == 0)
+    atomicOr(status, (unsigned)ST_DEGENERATE);
+  if (it.r0 == 0 && threadIdx.x == 0 && n >= 2) {
     double g = INFINITY;
     for (int k = 0; k + 1 < n; ++k) g = fmin(g, lam[k + 1] - lam[k]);
     const double sc = fmax(fabs(lam[0]), fabs(lam[n - 1]));
@@ -127,13 +134,13 @@ cudaError_t preload_identity() {
   return e;
 }
 
-cudaError_t launch_denominators(const DenomTask* tasks, int ntasks, int max_n, unsigned* status,
-                                cudaStream_t s) {
-  if (ntasks <= 0) return cudaSuccess;
+cudaError_t launch_denominators(const DenomTask* tasks, const DenomItem* items, int nitems,
+                                int max_n, unsigned* status, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
   const size_t smem = (size_t)max_n * sizeof(double);
   cudaError_t e = raise_smem_limit_once((const void*)k_denominators, g_denom_limit_set);
   if (e != cudaSuccess) return e;
-  k_denominators<<<ntasks, 256, smem, s>>>(tasks, status);
+  k_denominators<<<nitems, kDenomThreads, smem, s>>>(tasks, items, status);
   return cudaGetLastError();
 }
 

@@ -77,8 +77,9 @@ struct TridiagLaunch {
 
 size_t tridiag_global_slot_doubles(int max_m);
 size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps);
+// hi: the high-occupancy build of the global-slot variant (warps 4 or 8 only).
 cudaError_t launch_tridiag(bool smem_path, int warps, int grid, const TridiagLaunch& L,
-                           cudaStream_t s);
+                           cudaStream_t s, bool hi = false);
 
 // ---------------------------------------------------------------- K-b bisect
 // Eigenvalues of one symmetric tridiagonal (d[m], e[m-1]).  With parent != nullptr
@@ -91,26 +92,40 @@ struct BisectTask {
   const double* parent;
   double* eig;
 };
-// A block's share of a task: eigenvalues [k0, k0 + blockDim.x).
+// A block's share of a task: eigenvalues [k0, k0 + blockDim.x).  With ntask > 1 the block
+// instead takes all eigenvalues of the ntask consecutive tasks task .. task + ntask - 1,
+// all of one size m with ntask * m <= kBisectThreads (lane t: task t / m, eigenvalue t % m):
+// small minors of one matrix share a block.
 struct BisectItem {
   int task;
   int k0;
+  int ntask = 1;
 };
 constexpr int kBisectThreads = 256;
+constexpr int kBisectMaxPack = 64;   // packed tasks per block (so m >= 4 when packing)
 cudaError_t launch_bisect(const BisectTask* tasks, const BisectItem* items, int nitems,
                           int max_m, unsigned* status, cudaStream_t s);
 
 // ---------------------------------------------------------------- K-c identity
-// D_i = prod_{k != i} |lam_i - lam_k| for every i of one problem, kept as a
-// mantissa dm[i] in [0.5, 1) (0 if degenerate) and a binary exponent de[i].
+// D_i = prod_{k != i} |lam_i - lam_k| for the requested eigen-indices i = rows[r] of
+// one problem, kept as a mantissa dm[i] in [0.5, 1) (0 if degenerate) and a binary
+// exponent de[i] (arrays indexed by i, n long).
 struct DenomTask {
   const double* lam;
   int n;
   double* dm;
   int* de;
+  const int* rows;
+  int nrows;
 };
-cudaError_t launch_denominators(const DenomTask* tasks, int ntasks, int max_n, unsigned* status,
-                                cudaStream_t s);
+// A block's share of a task: rows [r0, r0 + kDenomThreads).
+struct DenomItem {
+  int task;
+  int r0;
+};
+constexpr int kDenomThreads = 256;
+cudaError_t launch_denominators(const DenomTask* tasks, const DenomItem* items, int nitems,
+                                int max_n, unsigned* status, cudaStream_t s);
 
 // One identity block: column c of one problem (minor eigenvalues mu[n-1]) for the
 // rows [r0, r0 + blockDim.x) of that problem's row list.

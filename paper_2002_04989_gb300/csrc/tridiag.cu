@@ -252,9 +252,13 @@ __device__ __forceinline__ void block_or_cluster_sync() {
 }
 
 // Minimum resident CTAs per SM the register allocation must allow.
-template <bool SMEM, int W>
+// HI: the high-occupancy build of the global-slot variant (at most 80 registers a thread:
+// three 8-warp or six 4-warp CTAs per SM, a little register spilling), for small matrices
+// whose per-step serial phases leave the FP64 pipe idle unless more CTAs share the SM.
+template <bool SMEM, int W, bool HI = false>
 struct MinBlocks {
-  static constexpr int value = (W >= 12) ? 1 : (W >= 8) ? 2 : (SMEM && W <= 2) ? 8 : 4;
+  static constexpr int value = HI ? ((W >= 8) ? 3 : 6)
+                                  : (W >= 12) ? 1 : (W >= 8) ? 2 : (SMEM && W <= 2) ? 8 : 4;
 };
 
 // CL = true: the cluster variant (global-slot path only).  One thread-block cluster of C
@@ -264,8 +268,8 @@ struct MinBlocks {
 // the same tile order and writes them into every CTA's shared copy of w (distributed
 // shared memory).  The serial phases (A-C, gamma, F) run redundantly in every CTA on
 // identical data.  So the results are bitwise those of the one-CTA global variant.
-template <bool SMEM, int W, bool CL = false>
-__global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W>::value)) k_tridiag(TridiagLaunch P) {
+template <bool SMEM, int W, bool CL = false, bool HI = false>
+__global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tridiag(TridiagLaunch P) {
   extern __shared__ __align__(16) double sm[];
   constexpr int NT = W * 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -559,17 +563,25 @@ std::atomic<uint64_t>& smem_limit_set() {
   return done;
 }
 
-template <bool SMEM, int W>
+template <bool SMEM, int W, bool HI = false>
 static cudaError_t launch_one(int grid, const TridiagLaunch& L, cudaStream_t s) {
   const size_t smem = tridiag_smem_bytes(SMEM, L.max_m, W);
-  cudaError_t e = raise_smem_limit_once((const void*)k_tridiag<SMEM, W>, smem_limit_set<SMEM, W>());
+  cudaError_t e = raise_smem_limit_once((const void*)k_tridiag<SMEM, W, false, HI>,
+                                        smem_limit_set<SMEM, W + (HI ? 200 : 0)>());
   if (e != cudaSuccess) return e;
-  k_tridiag<SMEM, W><<<grid, W * 32, smem, s>>>(L);
+  k_tridiag<SMEM, W, false, HI><<<grid, W * 32, smem, s>>>(L);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tridiag(bool smem_path, int warps, int grid, const TridiagLaunch& L,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool hi) {
+  if (hi && !smem_path) {
+    switch (warps) {
+      case 4: return launch_one<false, 4, true>(grid, L, s);
+      case 8: return launch_one<false, 8, true>(grid, L, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   if (smem_path) {
     switch (warps) {
       case 1: return launch_one<true, 1>(grid, L, s);
@@ -685,16 +697,32 @@ cudaError_t preload_tridiag() {
   EEID_PRE(true, 1) EEID_PRE(true, 2) EEID_PRE(true, 4) EEID_PRE(true, 8)
   EEID_PRE(false, 2) EEID_PRE(false, 4) EEID_PRE(false, 8) EEID_PRE(false, 12) EEID_PRE(false, 16)
 #undef EEID_PRE
+  if (e == cudaSuccess)
+    e = raise_smem_limit_once((const void*)k_tridiag<false, 4, false, true>, smem_limit_set<false, 204>());
+  if (e == cudaSuccess)
+    e = raise_smem_limit_once((const void*)k_tridiag<false, 8, false, true>, smem_limit_set<false, 208>());
   if (e == cudaSuccess) e = prepare_cluster_kernel<8>();
   if (e == cudaSuccess) e = prepare_cluster_kernel<12>();
   if (e == cudaSuccess) e = prepare_cluster_kernel<16>();
   return e;
 }
 
-int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m) {
+int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m, bool hi) {
   const size_t smem = tridiag_smem_bytes(smem_path, max_m, warps);
   int nb = 0;
   cudaError_t e = cudaErrorInvalidValue;
+  if (hi && !smem_path) {
+    if (warps == 4) {
+      e = raise_smem_limit_once((const void*)k_tridiag<false, 4, false, true>, smem_limit_set<false, 204>());
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tridiag<false, 4, false, true>, 128, smem);
+    } else if (warps == 8) {
+      e = raise_smem_limit_once((const void*)k_tridiag<false, 8, false, true>, smem_limit_set<false, 208>());
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tridiag<false, 8, false, true>, 256, smem);
+    }
+    return e == cudaSuccess ? nb : 0;
+  }
 #define EEID_OCC(S_, W_)                                                                   \
   if (smem_path == S_ && warps == W_) {                                                    \
     e = raise_smem_limit_once((const void*)k_tridiag<S_, W_>, smem_limit_set<S_, W_>());    \

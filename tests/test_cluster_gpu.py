@@ -90,3 +90,20 @@ def test_single_component_n4002(torch_cuda, ctx):
     print(f"n=4002 one component: cluster plan {times[True]:.3f} s, one CTA per matrix "
           f"{times[False]:.3f} s")
     assert times[True] < 0.5 * times[False]
+
+
+def test_cluster_rounds_bitwise_and_closed_form(torch_cuda, ctx):
+    """A uniform group with more matrices than half the SMs and a short last round
+    (n = 2001 with 199 columns: 200 reductions of m = 2000/2001, one CTA per SM) runs as
+    whole rounds of two-CTA clusters plus a last launch of clusters: bitwise equal to the
+    one-CTA plan, and within the bar of Q o Q."""
+    torch = torch_cuda
+    n = 2001
+    p = inputs.planted(n, 2001, -1.0, 1.0, 1e-4)
+    A = torch.from_numpy(p.A).cuda()
+    cols = np.sort(np.random.default_rng(7).choice(n, 199, replace=False))
+    rows = np.unique(np.r_[0, 1000, n - 1, np.random.default_rng(8).choice(n, 20, replace=False)])
+    got_c, lam_c = run(torch, ctx, A, rows, cols, True)
+    got_p, lam_p = run(torch, ctx, A, rows, cols, False)
+    assert np.array_equal(got_c, got_p) and np.array_equal(lam_c, lam_p)
+    assert np.max(np.abs(got_c - (p.Q * p.Q).T[np.ix_(rows, cols)])) <= TOL_VSQ

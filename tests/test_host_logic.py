@@ -19,6 +19,7 @@ DRIVER = r"""
 #include <cstring>
 #include <vector>
 #include <random>
+#include <algorithm>
 using namespace eeid;
 int main(int argc, char** argv) {
   if (!strcmp(argv[1], "plan")) {
@@ -29,6 +30,21 @@ int main(int argc, char** argv) {
     printf("%d %d %d %d\n", p.hybrid ? 1 : 0, p.bulk_grid, p.tail_at, p.tail_grid);
   } else if (!strcmp(argv[1], "cluster")) {
     printf("%d\n", cluster_size_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])));
+  } else if (!strcmp(argv[1], "crounds")) {
+    // nt sms m a2 a4 a8 a16 t_single
+    int act[4] = {atoi(argv[5]), atoi(argv[6]), atoi(argv[7]), atoi(argv[8])};
+    ClusterRounds r = plan_cluster_rounds(atoi(argv[2]), atoi(argv[3]), atoi(argv[4]), act, atof(argv[9]));
+    printf("%d %d %d %d %.4f\n", r.c1, r.per_round, r.bulk, r.c2, r.t);
+  } else if (!strcmp(argv[1], "bblocks")) {
+    // sizes of tasks 0..k-1 follow; order = every task, largest first (stable)
+    std::vector<int> m;
+    for (int i = 2; i < argc; ++i) m.push_back(atoi(argv[i]));
+    std::vector<int> order(m.size());
+    for (size_t i = 0; i < m.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return m[a] > m[b]; });
+    std::vector<BisectBlock> out;
+    plan_bisect_blocks(order, [&](int t) { return m[t]; }, 256, 64, out);
+    for (auto& b : out) printf("%d %d %d\n", b.task, b.k0, b.ntask);
   } else if (!strcmp(argv[1], "band")) {
     printf("%d\n", cost_band(atoll(argv[2]), atoll(argv[3])));
   } else if (!strcmp(argv[1], "pool")) {
@@ -181,3 +197,66 @@ def test_cluster_plan(driver):
             assert k == 16 or nt * 2 * k > sms       # the largest such power of two
         else:
             assert 2 * nt > sms
+
+
+def test_cluster_rounds(driver):
+    def cr(nt, sms=152, m=4095, act=(76, 38, 19, 9), t_single=None):
+        if t_single is None:
+            t_single = float(-(-nt // sms))
+        c1, per, bulk, c2, t = driver("crounds", nt, sms, m, *act, t_single)
+        return int(c1), int(per), int(bulk), int(c2), float(t)
+    # n = 4096 with 256 columns: 257 reductions, two one-CTA rounds (105 in the second);
+    # three rounds of 76 pairs, then the last 29 on clusters of 4 (116 SMs)
+    c1, per, bulk, c2, t = cr(257)
+    assert (c1, per, bulk, c2) == (2, 76, 228, 4) and t < 0.95 * 2
+    # a group that fills its rounds exactly gains nothing from clusters
+    assert cr(304)[0] == 0
+    # smaller matrices: the redundant per-step phases cost more, so 1025 reductions of
+    # m = 1023 stay with the one-CTA plan (whose pair-rounds are 6.67 rounds' time)
+    assert cr(1025, m=1023, t_single=3 * 1.89 + 1)[0] == 0
+    # below the size floor, never
+    assert cr(257, m=300)[0] == 0
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        nt = int(rng.integers(77, 1200))
+        m = int(rng.integers(384, 4097))
+        act = tuple(int(x) for x in (76, 38, 19, 9))
+        c1, per, bulk, c2, t = cr(nt, m=m, act=act)
+        if c1:
+            assert c1 in (2, 4) and per == act[c1 // 2 - 1] and bulk % per == 0
+            assert 0 < bulk <= nt and nt - bulk < per
+            assert c2 == 0 or ((nt - bulk) * c2 <= 152 and c2 & (c2 - 1) == 0)
+            assert t < 0.95 * -(-nt // 152)
+
+
+def test_bisect_blocks(driver):
+    """Minors of one matrix (consecutive tasks of one size) share bisection blocks; every
+    eigenvalue of every task is covered exactly once; no block exceeds 256 lanes."""
+    def blocks(sizes):
+        out = driver("bblocks", *sizes)
+        return [tuple(map(int, out[i:i + 3])) for i in range(0, len(out), 3)]
+    # an A of 8 and its 8 minors of 7: A alone (8 lanes), the minors in one block
+    assert blocks([8] + [7] * 8) == [(0, 0, 1), (1, 0, 8)]
+    # 300 minors of 3 (too small to pack) and a 600 task split in 256-lane blocks
+    b = blocks([600] + [3] * 2)
+    assert b == [(0, 0, 1), (0, 256, 1), (0, 512, 1), (1, 0, 1), (2, 0, 1)]
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        sizes = []
+        for _ in range(int(rng.integers(1, 6))):     # a few "matrices": A then its minors
+            n = int(rng.integers(2, 300))
+            sizes += [n] + [n - 1] * int(rng.integers(0, n + 1))
+        covered = {}
+        for t, k0, nt in blocks(sizes):
+            m = sizes[t]
+            if nt > 1:
+                assert nt * m <= 256 and nt <= 64 and m >= 4 and k0 == 0
+                assert all(sizes[t + q] == m for q in range(nt))
+                for q in range(nt):
+                    for k in range(m):
+                        covered[(t + q, k)] = covered.get((t + q, k), 0) + 1
+            else:
+                for k in range(k0, min(m, k0 + 256)):
+                    covered[(t, k)] = covered.get((t, k), 0) + 1
+        want = {(t, k) for t, m in enumerate(sizes) for k in range(m)}
+        assert set(covered) == want and all(v == 1 for v in covered.values())

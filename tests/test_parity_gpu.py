@@ -319,7 +319,7 @@ def test_autotune_table_and_cache(torch_cuda, tmp_path, oracle_mod):
     try:
         c1.eeid_autotune(256, path)
         lines = open(path).read().splitlines()
-        assert lines[0].startswith("eeid-tune v1") and len(lines) > 3
+        assert lines[0].startswith("eeid-tune v2") and len(lines) > 3
         assert int(lines[-1].split()[1]) >= 256
         c2.eeid_autotune(256, path)              # loads the cached table
         o1 = c1.eeid_components(dev(torch_cuda, A)).cpu().numpy()
@@ -393,12 +393,12 @@ def test_autotune_rejects_foreign_cache(torch_cuda, tmp_path):
     """A cache written for another device model is ignored (re-tuned and rewritten)."""
     from paper_2002_04989_gb300 import eeid
     path = tmp_path / "tune.txt"
-    path.write_text("eeid-tune v1 sms=1 name=Some Other GPU\n1 4096 1 4\n")
+    path.write_text("eeid-tune v2 sms=1 name=Some Other GPU\n1 4096 1 4\n")
     c = eeid.Context(0)
     try:
         c.eeid_autotune(64, str(path))
         head = path.read_text().splitlines()[0]
-        assert "Some Other GPU" not in head and head.startswith("eeid-tune v1")
+        assert "Some Other GPU" not in head and head.startswith("eeid-tune v2")
     finally:
         c.close()
 
@@ -555,3 +555,21 @@ def test_status_is_per_stream(torch_cuda, ctx):
     assert ctx.eeid_sync(s2) == eeid.EEID_WARN_SMALL_GAP
     assert ctx.eeid_sync(s1) == eeid.EEID_WARN_DEGENERATE
     assert ctx.eeid_sync(s1) == eeid.EEID_OK and ctx.eeid_sync(s2) == eeid.EEID_OK
+
+
+def test_high_occupancy_build_bitwise(torch_cuda):
+    """The high-occupancy build of the global-slot variant (path 2: 80 registers, more
+    CTAs per SM) runs the same arithmetic as path 1: bitwise the same grid."""
+    from paper_2002_04989_gb300 import eeid
+    torch = torch_cuda
+    dA = dev(torch, inputs.goe(230, 41))
+    outs = []
+    for path, W in ((1, 8), (2, 8), (2, 4)):
+        c = eeid.Context(0)
+        try:
+            c.eeid_tune_tridiag(161, 2048, path, W)
+            outs.append(c.eeid_components(dA).cpu().numpy())
+            c.eeid_sync()
+        finally:
+            c.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])

@@ -64,9 +64,12 @@ def test_served_results_against_oracle_and_closed_form(torch_cuda, oracle_mod):
     requests (n from 40 to 1300, so the 16-warp reductions and round-sized launches
     of n > 1024 are covered) against the closed form Q o Q, GOE requests against the
     long-double oracle.  Requests go in together, so they share batches and overlap."""
-    planted = [inputs.planted(n, 900 + n, -1.0, 1.0, 1e-4) for n in (40, 200, 520, 1100, 1300)]
+    planted = [inputs.planted(n, 900 + n, -1.0, 1.0, 1e-4) for n in (40, 200, 520, 1100, 1300, 1200)]
     goes = [inputs.goe(n, 950 + n) for n in (24, 61, 90)]
-    col_sets = [None, np.array([0, 7, 39]), None, np.array([3, 500, 1099]), np.arange(0, 1300, 97)]
+    # the n = 1200 request with 199 columns has 200 reductions: whole rounds and a short
+    # remainder that runs as one launch of clusters
+    col_sets = [None, np.array([0, 7, 39]), None, np.array([3, 500, 1099]), np.arange(0, 1300, 97),
+                np.sort(np.random.default_rng(12).choice(1200, 199, replace=False))]
     with eeid.Server(0, max_batch=8, max_inflight=2) as srv:
         tp = [srv.eeid_server_submit(p.A, cols=c) for p, c in zip(planted, col_sets)]
         tg = [srv.eeid_server_submit(A) for A in goes]
