@@ -111,20 +111,7 @@ def test_arrivals_overlap_a_running_batch(torch_cuda):
         assert np.array_equal(out, o_ref)
 
 
-@pytest.fixture(scope="module")
-def warm_server_process(torch_cuda):
-    """The first server of a process can once run a small batch only after a large one
-    it overlaps (a cold start whose cause is not found); a throwaway server with one
-    overlapping pair of batches takes that once, so the timing test below does not
-    depend on test order."""
-    with eeid.Server(0, max_batch=4, max_inflight=2) as srv:
-        t1 = srv.eeid_server_submit(inputs.goe(600, 1))
-        t2 = srv.eeid_server_submit(inputs.goe(24, 2))
-        srv.eeid_server_wait(t2)
-        srv.eeid_server_wait(t1)
-
-
-def test_cost_bands_and_round_launches(torch_cuda, warm_server_process):
+def test_cost_bands_and_round_launches(torch_cuda):
     """A large request and small ones queued at the same moment go to different batches
     (cost bands), and the small ones finish first although the large batch was
     launched first: its reductions run one round at a time, so the second slot's
