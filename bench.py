@@ -666,12 +666,35 @@ def run_profile_case(case: str) -> int:
     matrix (one / two CTAs per SM), called twice (its k_bisect, k_denominators and
     k_identity launches are the ones captured for those kernels); batch256 = the
     matrices of the uneven batch with n in (192, 256] (316 of them) in one batched call
-    with the autotuned variants, graphs off, called twice."""
+    with the autotuned variants, graphs off, called twice; single2002 = one component of
+    a planted n = 2002 matrix (the cluster plan), called twice; herm512 = a complex
+    Hermitian n = 512 matrix with 151 columns, called twice."""
     import numpy as np
     import torch
 
     from paper_2002_04989_gb300 import eeid, inputs
     ctx = eeid.Context(0)
+    if case == "single2002":
+        # one component of a planted n = 2002 matrix: A and one minor, two clusters of 16
+        pl = inputs.planted(2002, 2002, -1.0, 1.0, 1e-4)
+        A = torch.from_numpy(pl.A).cuda()
+        for _ in range(2):
+            out = ctx.eeid_components(A, rows=[700], cols=[1500])
+            ctx.eeid_sync()
+        err = abs(float(out.cpu().numpy()[0, 0]) - pl.Q[1500, 700] ** 2)
+        print(f"{case}: abs err vs Q o Q = {err:.3e}")
+        return 0 if err <= 1e-10 else 1
+    if case == "herm512":
+        # complex Hermitian n = 512, 151 columns: 152 reductions, one CTA per SM
+        pl = inputs.planted_herm(512, 512, -1.0, 1.0, 1e-4)
+        A = torch.from_numpy(pl.A).cuda()
+        cols = np.arange(151)
+        for _ in range(2):
+            out = ctx.eeid_components_herm(A, cols=cols)
+            ctx.eeid_sync()
+        err = float(np.max(np.abs(out.cpu().numpy() - (np.abs(pl.Q) ** 2).T[:, cols])))
+        print(f"{case}: max abs err vs |Q|^2 = {err:.3e}")
+        return 0 if err <= 1e-10 else 1
     if case == "batch256":
         tune_path = os.path.join(ROOT, "paper_2002_04989_gb300", "_build", "tune_table.txt")
         ctx.eeid_autotune(256, tune_path)
@@ -718,7 +741,8 @@ def main(argv=None):
                     help="serving: length of the prefix of the seeded request stream")
     ap.add_argument("--serving-rates", default="0.5,1,2",
                     help="serving: comma-separated Poisson arrival rates (requests/s)")
-    ap.add_argument("--profile-case", choices=("tridiag152", "tridiag304", "batch256"), default=None,
+    ap.add_argument("--profile-case", choices=("tridiag152", "tridiag304", "batch256", "single2002",
+                                               "herm512"), default=None,
                     help="run only a small case for an ncu capture and exit: tridiag152 / "
                          "tridiag304 = A plus the first 151 / 303 minors of the planted "
                          "n=1024 matrix (one / two CTAs per SM), called twice")

@@ -161,7 +161,10 @@ void finalize(eeid_server* S, Slot& sl, std::unique_lock<std::mutex>& lk, cudaEr
 
 // Batches from this band up (about 0.2 s of reductions and more) leave 1/16 of the SMs
 // free of their persistent reduction CTAs, which take a whole SM each: a smaller batch
-// launched meanwhile runs there at once instead of waiting for round boundaries.
+// launched meanwhile runs there at once instead of waiting for round boundaries.  The
+// reserve is kept only while other work is around (requests waiting, or another batch on
+// the GPU); a costly batch that arrives to an idle server takes every SM, and a request
+// that arrives later waits at most for the end of one of its rounds.
 constexpr int kReserveBand = 3;
 // Pinned staging pool for requests, and each slot's pinned metadata stage.
 constexpr size_t kPinnedPoolBytes = (size_t)1 << 30;
@@ -199,6 +202,8 @@ bool launch(eeid_server* S, Slot& sl, std::unique_lock<std::mutex>& lk) {
     batch.push_back(r);
   }
   if (batch.empty()) return false;
+  bool others = !S->pending.empty();
+  for (auto& x : S->slots) others |= (&x != &sl && x.busy);
   S->cv_space.notify_all();
   const int64_t bid = S->next_batch++;
   const auto now = Clock::now();
@@ -236,7 +241,8 @@ bool launch(eeid_server* S, Slot& sl, std::unique_lock<std::mutex>& lk) {
   }
   eeid_status st = EEID_OK;
   if (e == cudaSuccess && S->slots.size() > 1)
-    st = eeid::set_sm_reserve(sl.ctx, band >= kReserveBand ? std::max(1, S->sms / 16) : 0);
+    st = eeid::set_sm_reserve(sl.ctx,
+                              band >= kReserveBand && others ? std::max(1, S->sms / 16) : 0);
   if (e == cudaSuccess && st == EEID_OK)
     st = eeid_components_batched(sl.ctx, probs.data(), (int64_t)probs.size(), sl.stream);
   if (e == cudaSuccess && st >= 0)
