@@ -129,9 +129,12 @@ eeid_status eeid_components_host(eeid_ctx* ctx, const double* hA, int64_t lda, i
  *     v_ij = (q_ij - (|v_ir|^2 + |v_ij|^2) / 2) / |v_ir|   (v_ir > 0).
  * References are chosen on the device by a greedy cover with |v_ir| >= max_j |v_ij| / 4,
  * so the error of v_ij is about 2 delta / |v_ir| <= 8 sqrt(n) delta, delta being the
- * error of |v_ij|^2.  Each reference costs one rotated minor per component (n - 1
- * reductions): a few eigenvectors often share one reference, a whole eigenbasis of a
- * random matrix needs about ten.
+ * error of |v_ij|^2.  Each reference costs one rotated minor per component j whose
+ * |v_ij|^2 is not exactly 0 for some row sharing it (at most n - 1 reductions); such
+ * exactly-zero components are returned as 0.  A few eigenvectors often share one
+ * reference, and a whole eigenbasis of a random matrix needs about ten.  Strongly
+ * localised eigenvectors (nearly decoupled blocks) may each need their own reference,
+ * up to n of them, so the cost grows toward n^2 reductions there.
  * Sign convention: the component of largest |v_ij|^2 (the first on exact ties) is
  * positive.  Rows of eigenvalues that are exactly degenerate are NaN.
  * h_rows: host, distinct indices in [0, n), NULL = all (nrows = n).  d_lambda_opt:

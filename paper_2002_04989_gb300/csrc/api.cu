@@ -27,10 +27,11 @@ int tridiag_herm_blocks_per_sm(int warps, int max_m);
 cudaError_t preload_vectors();
 size_t pick_refs_smem_bytes(int nrows, int n);
 cudaError_t launch_pick_refs(const double* g, int nrows, int n, int* refs, int* row_ref,
-                             int* nref, cudaStream_t s);
+                             int* nref, unsigned char* need, cudaStream_t s);
 cudaError_t launch_signed(const void* rows, int nrows, int n, cudaStream_t s);
 size_t signed_row_bytes();
-void fill_signed_row(void* dst, const double* g, const double* q, double* out, int ref);
+void fill_signed_row(void* dst, const double* g, const double* q, const int* pos, double* out,
+                     int ref);
 }
 
 using namespace eeid;
@@ -1413,6 +1414,8 @@ eeid_status eeid_eigenvectors(eeid_ctx* ctx, const double* dA, int64_t lda, int6
   const size_t l_off = ar.take(sizeof(double) * N);
   const size_t r_off = ar.take(sizeof(int) * (1 + 2 * (size_t)NR));
   const size_t s_off = ar.take(signed_row_bytes() * NR);
+  const size_t n_off = ar.take((size_t)NR * N);                 // need[R][N] (R <= NR)
+  const size_t p_off = ar.take(sizeof(int) * (size_t)NR * N);   // colpos[R][N]
   if (ar.off > ctx->budget)
     return fail(EEID_ERR_NOMEM, "eigenvector buffers of %zu bytes exceed the HBM budget", ar.off);
   if (ar.off > ctx->vbuf_cap) {
@@ -1429,7 +1432,8 @@ eeid_status eeid_eigenvectors(eeid_ctx* ctx, const double* dA, int64_t lda, int6
     }
     ctx->vbuf_cap = ar.off;
   }
-  const size_t h_bytes = std::max(sizeof(int) * (1 + 2 * (size_t)NR), signed_row_bytes() * NR);
+  const size_t h_bytes = std::max({sizeof(int) * (1 + 2 * (size_t)NR), (size_t)NR * N,
+                                   signed_row_bytes() * NR + sizeof(int) * (size_t)NR * N});
   if (ctx->vec_used) EEID_CK(cudaEventSynchronize(ctx->vec_ev), "cudaEventSynchronize(vectors)");
   if (!ctx->vec_ev) EEID_CK(cudaEventCreateWithFlags(&ctx->vec_ev, cudaEventDisableTiming), "event");
   if (h_bytes > ctx->h_vec_cap) {
@@ -1444,6 +1448,8 @@ eeid_status eeid_eigenvectors(eeid_ctx* ctx, const double* dA, int64_t lda, int6
   double* Qg = (double*)(vb + q_off);
   double* lam = d_lambda_opt ? d_lambda_opt : (double*)(vb + l_off);
   int* ri = (int*)(vb + r_off);   // [nref | refs[NR] | row_ref[NR]]
+  unsigned char* need = (unsigned char*)(vb + n_off);
+  int* colpos = (int*)(vb + p_off);
 
   // ---- phase 1: |v_ij|^2 for the requested rows, all components j (Eq. 1)
   std::vector<Problem> p1(1);
@@ -1457,7 +1463,7 @@ eeid_status eeid_eigenvectors(eeid_ctx* ctx, const double* dA, int64_t lda, int6
   st = run(ctx, p1, MODE_COMPONENTS, s);
   if (st != EEID_OK) return st;
   // ---- phase 2: references (greedy cover on the device), read back to plan phase 3
-  EEID_CK(launch_pick_refs(G, NR, N, ri + 1, ri + 1 + NR, ri, s), "pick_refs launch");
+  EEID_CK(launch_pick_refs(G, NR, N, ri + 1, ri + 1 + NR, ri, need, s), "pick_refs launch");
   ctx->launches++;
   int* h_ri = (int*)ctx->h_vec;
   EEID_CK(cudaMemcpyAsync(h_ri, ri, sizeof(int) * (1 + 2 * (size_t)NR), cudaMemcpyDeviceToHost, s),
@@ -1467,37 +1473,58 @@ eeid_status eeid_eigenvectors(eeid_ctx* ctx, const double* dA, int64_t lda, int6
   if (R < 0 || R > NR) return fail(EEID_ERR_CUDA, "reference selection returned %d", R);
   std::vector<int> refs(h_ri + 1, h_ri + 1 + R), row_ref(h_ri + 1 + NR, h_ri + 1 + 2 * NR);
   ctx->vec_refs = R;
-  // ---- phase 3: one problem per reference r: the rotated minors (r, j), j != r, for
-  // the rows that chose r
-  std::vector<Problem> p3(R);
-  std::vector<size_t> q_base(R, 0);
+  // the columns each reference's rows need (|v_ij|^2 not exactly 0 for one of them)
+  std::vector<unsigned char> h_need((size_t)R * N);
+  if (R > 0) {
+    EEID_CK(cudaMemcpyAsync(ctx->h_vec, need, (size_t)R * N, cudaMemcpyDeviceToHost, s),
+            "cudaMemcpyAsync(columns needed)");
+    EEID_CK(cudaStreamSynchronize(s), "cudaStreamSynchronize(columns needed)");
+    memcpy(h_need.data(), ctx->h_vec, (size_t)R * N);
+  }
+  // ---- phase 3: one problem per reference r: the rotated minors (r, j) for the columns
+  // j != r its rows need, for the rows that chose r
+  std::vector<Problem> p3;
+  std::vector<size_t> q_base(R, 0), q_ncols(R, 0);
   std::vector<int> pos(NR, -1);
+  std::vector<int> h_colpos((size_t)R * N, -1);
   size_t qoff = 0;
   for (int q = 0; q < R; ++q) {
-    Problem& P = p3[q];
+    Problem P;
     for (int r = 0; r < NR; ++r)
       if (row_ref[r] == q) { pos[r] = (int)P.rows.size(); P.rows.push_back(rows[r]); }
     for (int j = 0; j < N; ++j)
-      if (j != refs[q]) P.cols.push_back(j);
-    P.dA = dA; P.lda = lda; P.n = N; P.rot = refs[q]; P.lam_in = lam;
-    P.out = Qg + qoff;
+      if (j != refs[q] && h_need[(size_t)q * N + j]) {
+        h_colpos[(size_t)q * N + j] = (int)P.cols.size();
+        P.cols.push_back(j);
+      }
     q_base[q] = qoff;
-    qoff += P.rows.size() * (size_t)(N - 1);
+    q_ncols[q] = P.cols.size();
+    qoff += P.rows.size() * P.cols.size();
+    if (P.cols.empty()) continue;   // every other component of these rows is exactly 0
+    P.dA = dA; P.lda = lda; P.n = N; P.rot = refs[q]; P.lam_in = lam;
+    P.out = Qg + q_base[q];
+    p3.push_back(std::move(P));
   }
-  if (N >= 2 && R > 0) {
+  if (N >= 2 && !p3.empty()) {
     st = run(ctx, p3, MODE_COMPONENTS, s);
     if (st != EEID_OK) return st;
   }
   // ---- phase 4: assemble the signed vectors and apply the sign convention
   char* h_rows_img = ctx->h_vec;
+  int* h_pos_img = (int*)(ctx->h_vec + signed_row_bytes() * NR);
   for (int r = 0; r < NR; ++r) {
     const int q = row_ref[r];
-    const double* qrow = q >= 0 ? Qg + q_base[q] + (size_t)pos[r] * (N - 1) : nullptr;
+    const double* qrow = q >= 0 ? Qg + q_base[q] + (size_t)pos[r] * q_ncols[q] : nullptr;
     fill_signed_row(h_rows_img + signed_row_bytes() * r, G + (size_t)r * N, qrow,
-                    d_vec + (size_t)r * N, q >= 0 ? refs[q] : -1);
+                    q >= 0 ? colpos + (size_t)q * N : nullptr, d_vec + (size_t)r * N,
+                    q >= 0 ? refs[q] : -1);
   }
+  if (R > 0) memcpy(h_pos_img, h_colpos.data(), sizeof(int) * (size_t)R * N);
   EEID_CK(cudaMemcpyAsync(vb + s_off, h_rows_img, signed_row_bytes() * NR, cudaMemcpyHostToDevice, s),
           "cudaMemcpyAsync(signed rows)");
+  if (R > 0)
+    EEID_CK(cudaMemcpyAsync(colpos, h_pos_img, sizeof(int) * (size_t)R * N, cudaMemcpyHostToDevice,
+                            s), "cudaMemcpyAsync(column positions)");
   EEID_CK(cudaEventRecord(ctx->vec_ev, s), "cudaEventRecord(vectors)");
   ctx->vec_used = true;
   EEID_CK(launch_signed(vb + s_off, NR, N, s), "signed launch");

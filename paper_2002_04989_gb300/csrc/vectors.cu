@@ -29,11 +29,13 @@ constexpr double kRefRatio = 1.0 / 16.0;
 
 // One CTA.  g: nrows x n (row r = |v_{i_r, j}|^2 for all j).  Outputs: refs[0 .. *nref)
 // (component indices), row_ref[r] (index into refs; -1 for a row with no usable
-// magnitude: all zero or NaN, i.e. a degenerate eigenvalue).  Scratch in shared memory:
-// thr (nrows doubles), covered (nrows bytes), count (n ints).
+// magnitude: all zero or NaN, i.e. a degenerate eigenvalue), and need[q*n + j] = 1 when
+// some row of reference q has |v_ij|^2 != 0 (a column whose magnitudes are exactly zero
+// for all of them needs no rotated minor: those components are exactly 0).  Scratch in
+// shared memory: thr (nrows doubles), covered (nrows bytes), count (n ints).
 __global__ void __launch_bounds__(kPickThreads)
 k_pick_refs(const double* __restrict__ g, int nrows, int n, int* __restrict__ refs,
-            int* __restrict__ row_ref, int* __restrict__ nref) {
+            int* __restrict__ row_ref, int* __restrict__ nref, unsigned char* __restrict__ need) {
   extern __shared__ __align__(16) double thr[];
   int* count = (int*)(thr + nrows);
   unsigned char* covered = (unsigned char*)(count + n);
@@ -109,13 +111,23 @@ k_pick_refs(const double* __restrict__ g, int nrows, int n, int* __restrict__ re
     __syncthreads();
   }
   if (tid == 0) *nref = R;
+  // columns each reference's rows need (row_ref complete after the last barrier)
+  for (int j = tid; j < n; j += kPickThreads) {
+    for (int q = 0; q < R; ++q) need[(size_t)q * n + j] = 0;
+    for (int r = 0; r < nrows; ++r) {
+      const int q = row_ref[r];
+      if (q >= 0 && g[(size_t)r * n + j] != 0.0) need[(size_t)q * n + j] = 1;
+    }
+  }
 }
 
 // One CTA per requested eigenvector.  g: its |v_ij|^2 row (n); q: its row of rotated
-// components q_ij for j != ref in increasing j (n - 1 values); out: the signed vector.
+// components; pos[j]: the place of q_ij in that row, or -1 where no rotated minor was
+// needed (|v_ij|^2 exactly 0 for every row of this reference); out: the signed vector.
 struct SignedRow {
   const double* g;
   const double* q;
+  const int* pos;
   double* out;
   int ref;   // reference component, -1 if the row had no usable magnitude
 };
@@ -162,17 +174,19 @@ k_signed(const SignedRow* __restrict__ rows, int n) {
   if (jstar == r) {
     vstar = vr;
   } else {
-    const double qs = R.q[jstar < r ? jstar : jstar - 1];
+    const double qs = R.q[R.pos[jstar]];   // |v_ij*|^2 > 0, so its minor was computed
     vstar = (qs - 0.5 * (gr + R.g[jstar])) / vr;
   }
   const double flip = vstar < 0.0 ? -1.0 : 1.0;
   for (int j = tid; j < n; j += kSignedThreads) {
     double v;
+    const int pj = R.pos[j];
     if (j == r) {
       v = vr;
+    } else if (pj < 0) {
+      v = 0.0;
     } else {
-      const double qj = R.q[j < r ? j : j - 1];
-      v = (qj - 0.5 * (gr + R.g[j])) / vr;
+      v = (R.q[pj] - 0.5 * (gr + R.g[j])) / vr;
     }
     R.out[j] = flip * v;
   }
@@ -191,11 +205,11 @@ cudaError_t preload_vectors() {
 }
 
 cudaError_t launch_pick_refs(const double* g, int nrows, int n, int* refs, int* row_ref,
-                             int* nref, cudaStream_t s) {
+                             int* nref, unsigned char* need, cudaStream_t s) {
   cudaError_t e = raise_smem_limit_once((const void*)k_pick_refs, g_pick_limit_set);
   if (e != cudaSuccess) return e;
   k_pick_refs<<<1, kPickThreads, pick_refs_smem_bytes(nrows, n), s>>>(g, nrows, n, refs, row_ref,
-                                                                      nref);
+                                                                      nref, need);
   return cudaGetLastError();
 }
 
@@ -207,8 +221,9 @@ cudaError_t launch_signed(const void* rows, int nrows, int n, cudaStream_t s) {
 
 size_t signed_row_bytes() { return sizeof(SignedRow); }
 
-void fill_signed_row(void* dst, const double* g, const double* q, double* out, int ref) {
-  SignedRow r{g, q, out, ref};
+void fill_signed_row(void* dst, const double* g, const double* q, const int* pos, double* out,
+                     int ref) {
+  SignedRow r{g, q, pos, out, ref};
   *(SignedRow*)dst = r;
 }
 

@@ -112,3 +112,17 @@ def test_batch_mixing_plans_bitwise(torch_cuda, ctx):
     ctx.eeid_sync()
     for pr, s in zip(probs, singles):
         assert np.array_equal(pr["out"].cpu().numpy(), s)
+
+
+def test_vectors_diagonal_one_reference_each(torch_cuda, ctx):
+    """A diagonal matrix (n = 300): every eigenvector is a unit vector, so each needs its
+    own reference (300 of them); components whose |v_ij|^2 came out exactly 0 need no
+    rotated minor.  The result is the permuted identity within the bar."""
+    d = np.random.default_rng(9).permutation(np.linspace(-2.0, 3.0, 300))
+    A = torch_cuda.from_numpy(np.diag(d)).cuda()
+    vec = ctx.eeid_eigenvectors(A).cpu().numpy()
+    ctx.eeid_sync()
+    assert ctx.eeid_vector_refs() == 300
+    ref = np.zeros((300, 300))
+    ref[np.arange(300), np.argsort(d)] = 1.0
+    assert np.max(np.abs(vec - ref)) <= TOL
