@@ -21,7 +21,8 @@
 // real global-slot kernel: 32 x 32 tiles split over the warps in contiguous ranges,
 // every tile keeping its own column partial (the strictly upper part, conj(a_ic) v_i)
 // and row partial (a_ic v_c, c <= i) in the CTA's global slot, summed in tile order, so
-// a matrix's (d, e) do not depend on the warp count.  Diagonal tiles are not packed.
+// a matrix's (d, e) do not depend on the warp count.  Diagonal tiles are packed (their
+// lower triangle in 17 full warp-rows, mirrored into the shared tile for the product).
 #include "internal.cuh"
 
 namespace eeid {
@@ -118,6 +119,63 @@ __device__ __forceinline__ void htile(double2* S, int64_t ld, int m, int R0, int
     const bool ok = !EDGE || (lane < nrows && C0 + cc <= i);
     const double2 x = ok ? tile[lane * kTP + cc] : z;
     mac(u, x, vC[C0 + cc]);
+  }
+  *uslot = u;
+  __syncwarp();
+}
+
+// Diagonal tile: its lower triangle is 528 of 1024 entries, so the lane-per-column
+// mapping of htile would issue with half the lanes masked.  The update is packed instead:
+// warp-row r < 15 holds row r (lanes 0..r) and row 30-r (lanes r+1..31), then row 15 and
+// row 31, 17 warp-rows in all.  Each updated entry a_ic goes to the shared tile at (i, c)
+// and its conjugate at (c, i); one pass over the full Hermitian tile then gives the whole
+// product row by row (row partials only; the tile's column partial is 0).
+template <bool UPD>
+__device__ __forceinline__ void hdiag(double2* S, int64_t ld, int m, int R0, int lane,
+                                      const double2* vP, const double2* wP, const double2* vC,
+                                      double2* tile, double2* tslot, double2* uslot) {
+  const double2 z = make_double2(0.0, 0.0);
+  const int nrows = min(kT, m - R0);
+#pragma unroll
+  for (int it = 0; it < 17; ++it) {
+    int i, c;
+    bool valid;
+    if (it < 15) {
+      const bool first = lane <= it;
+      i = first ? it : 30 - it;
+      c = first ? lane : lane - it - 1;
+      valid = true;
+    } else if (it == 15) {
+      i = 15;
+      c = lane;
+      valid = lane <= 15;
+    } else {
+      i = 31;
+      c = lane;
+      valid = true;
+    }
+    valid = valid && i < nrows;
+    double2* ptr = S + (size_t)(R0 + i) * ld + (R0 + c);
+    double2 a = valid ? *ptr : z;
+    if (UPD) {
+      double2 x = rank2(a, vP[R0 + i], wP[R0 + c], wP[R0 + i], vP[R0 + c]);
+      if (i == c) x.y = 0.0;
+      a = valid ? x : z;
+      if (valid) *ptr = a;
+    }
+    if (valid) {
+      tile[i * kTP + c] = a;
+      tile[c * kTP + i] = make_double2(a.x, -a.y);
+    }
+  }
+  *tslot = z;
+  __syncwarp();
+  double2 u = z;
+#pragma unroll 8
+  for (int cc = 0; cc < kT; ++cc) {
+    const bool ok = lane < nrows && cc < nrows;
+    const double2 x = ok ? tile[lane * kTP + cc] : z;
+    mac(u, x, vC[R0 + cc]);
   }
   *uslot = u;
   __syncwarp();
@@ -251,6 +309,9 @@ __global__ void __launch_bounds__(W * 32, 1) k_tridiag_herm(TridiagLaunch P) {
           if (J < I && R0 + kT <= m) {
             if (upd) htile<false, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, uslot);
             else     htile<false, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, uslot);
+          } else if (J == I) {
+            if (upd) hdiag<true>(S, ld, m, R0, lane, vP, wP, vC, tile, tslot, uslot);
+            else     hdiag<false>(S, ld, m, R0, lane, vP, wP, vC, tile, tslot, uslot);
           } else {
             if (upd) htile<true, true>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, uslot);
             else     htile<true, false>(S, ld, m, R0, C0, lane, vP, wP, vC, tile, tslot, uslot);
