@@ -383,6 +383,7 @@ def workload_record(name, ctx, dev, stream, steps, warmup, local=0):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     rec = {}
     plain_step = None
+    extra_steps = {}   # label -> another plan of the same step, timed once after the run
     phase_timed = True
     if name == "batch4096":
         # per-size kernel variants picked by the autotuner (cached per device model)
@@ -455,12 +456,19 @@ def workload_record(name, ctx, dev, stream, steps, warmup, local=0):
             flush.fill_(1)
 
         def plain_step():
-            ctx.eeid_set_clusters(False)
+            ctx.eeid_set_clusters(0)
             step()
-            ctx.eeid_set_clusters(True)
+            ctx.eeid_set_clusters(2)
+
+        def cluster_step():
+            ctx.eeid_set_clusters(1)
+            step()
+            ctx.eeid_set_clusters(2)
+        extra_steps["cluster_plan_16_ctas_per_matrix"] = cluster_step
         workload = ("single4002: one component |v_ij|^2 (i=1234, j=2001) of a planted FP64 "
-                    "n=4002 matrix: A and one minor, cluster plan (latency mode); the paper's "
-                    "Table 1 task at n=4002 took 16.78 s on a 4-core Xeon (context only)")
+                    "n=4002 matrix: A and one minor, group plan (latency mode: each reduction "
+                    "on 76 CTAs); the paper's Table 1 task at n=4002 took 16.78 s on a 4-core "
+                    "Xeon (context only)")
     elif name == "herm1024":
         pl = inputs.planted_herm(1024, inputs.seed_for(inputs.CFG_PLANTED1024, 7))
         A = torch.from_numpy(pl.A).to(dev)
@@ -518,6 +526,10 @@ def workload_record(name, ctx, dev, stream, steps, warmup, local=0):
         plain_step()
         pm = _timed(torch, stream, plain_step, 1)
         key = "one_cta_per_matrix" if name == "single4002" else "plain_one_call_per_matrix"
+        rec[key] = {"value": units / (pm / 1e3), "ms_per_step": pm}
+    for key, fn in extra_steps.items():
+        fn()
+        pm = _timed(torch, stream, fn, 1)
         rec[key] = {"value": units / (pm / 1e3), "ms_per_step": pm}
     if phase_avg:
         roof = alu_roofline(flops, phase_avg.get("tridiag", 0.0),

@@ -199,15 +199,31 @@ eeid_status eeid_set_graphs(eeid_ctx* ctx, int enable);
  * overlap. */
 eeid_status eeid_set_overlap(eeid_ctx* ctx, int enable);
 
-/* Enable (default) or disable the cluster plan (latency mode).  When a call has few
+/* Latency mode: the cluster and group plans (both on by default).  When a call has few
  * Householder reductions (at most half as many as the device has SMs: one or a few
  * components, a few columns, or the eigenvalues of one large A -- the single-component
  * tasks of the paper's Table 1) of matrices with m >= 384, each reduction runs on a
  * thread-block cluster of up to 16 CTAs on as many SMs instead of on one CTA: the tiles
  * of every column step are split over the cluster, partial sums stay in the matrix's
  * workspace slot and the step vectors are exchanged through distributed shared memory.
- * Results are bitwise the same either way. */
-eeid_status eeid_set_clusters(eeid_ctx* ctx, int enable);
+ * When there are so few reductions of m >= 1536 that G = SMs / reductions exceeds 16
+ * (one component of a large A: two reductions), the group plan runs each on G CTAs
+ * launched cooperatively (all resident at once), which exchange the step vectors through
+ * global memory and meet at bounded global-memory barriers.  A barrier that waits beyond
+ * its limit (one second; only if the CTAs were not resident together) makes the group
+ * stop, leaving its output incomplete, and eeid_sync return EEID_ERR_TIMEOUT.
+ * mode 0 = both off; 1 = the cluster plan only; 2 (default) = both.  Results are bitwise
+ * the same in every mode. */
+eeid_status eeid_set_clusters(eeid_ctx* ctx, int mode);
+
+/* Self-test of the bounded barrier wait of the group plan (see eeid_set_clusters): runs
+ * the group variant of K-a on a 2 x 2 matrix as a group of two CTAs of which only one is
+ * launched, so the group's first barrier never fills.  The launched CTA gives up after
+ * the wait limit (one second of the GPU's global timer) and sets the timeout bit of
+ * `stream`'s status word; the call returns once the stream is idle, and the next
+ * eeid_sync(ctx, stream) returns EEID_ERR_TIMEOUT.  The context stays usable.  Takes a
+ * little over a second. */
+eeid_status eeid_check_barrier_timeout(eeid_ctx* ctx, void* stream);
 
 /* Number of kernel launches the context has enqueued so far (for accounting). */
 int64_t eeid_launch_count(const eeid_ctx* ctx);
@@ -353,8 +369,10 @@ enum {
   EEID_DEV_BRACKET_FALLBACK = 4u, /* a bisection bracket failed its check and restarted from
                                      the Gershgorin bracket (information only: the result
                                      is still correct) */
-  EEID_DEV_BAD_TASK = 8u          /* a kernel met a matrix beyond its size limit and skipped
+  EEID_DEV_BAD_TASK = 8u,         /* a kernel met a matrix beyond its size limit and skipped
                                      it: the output for that matrix was not written */
+  EEID_DEV_TIMEOUT = 16u          /* a cooperative reduction's barrier wait ran out (group
+                                     plan only): its group stopped, its output is invalid */
 };
 
 /* Eigenvalues of A, like eeid_eigvals, for callers that cannot allocate device

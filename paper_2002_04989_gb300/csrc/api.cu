@@ -19,6 +19,10 @@ int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m, bool hi);
 cudaError_t launch_tridiag_cluster(int warps, int nclusters, int csize, const TridiagLaunch& L,
                                    cudaStream_t s);
 int tridiag_max_active_clusters(int warps, int csize, int max_m);
+cudaError_t launch_tridiag_group(int warps, int ngroups, int group, const TridiagLaunch& L,
+                                 cudaStream_t s);
+int tridiag_group_blocks_per_sm(int warps, int max_m);
+cudaError_t launch_tridiag_group_short(const TridiagLaunch& L, cudaStream_t s);
 size_t tridiag_herm_slot_doubles(int max_m);
 size_t tridiag_herm_smem_bytes(int max_m, int warps);
 cudaError_t launch_tridiag_herm(int warps, int grid, const TridiagLaunch& L, cudaStream_t s);
@@ -123,8 +127,10 @@ struct eeid_ctx {
   bool round_launches = false;
   // SMs the persistent reductions leave free (serving: room for a second batch).
   int sm_reserve = 0;
-  // Cluster plan for groups of few large reductions (see cluster_size_for).
+  // Cluster plan for groups of few large reductions (see cluster_size_for), and the group
+  // plan for the fewest largest (see group_size_for).
   bool clusters_enabled = true;
+  bool groups_enabled = true;
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   bool timing = false;
@@ -436,7 +442,8 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     groups[cfg_key(probs[tri[t].prob].herm ? herm_cfg(tri[t].m) : tri_cfg(ctx, tri[t].m))]
         .push_back((int)t);
   struct GroupPlan { TriCfg cfg; int max_m; int grid; int nchunks; size_t task_off, counter_off,
-                     work_off; size_t slot; std::vector<int> idx; int csize = 0; };
+                     work_off; size_t slot; std::vector<int> idx; int csize = 0; int gsize = 0;
+                     size_t gsync_off = 0, gw_off = 0; };
   std::vector<GroupPlan> gplans;
   for (int key = 0; key < 128; ++key) {
     if (groups[key].empty()) continue;
@@ -484,7 +491,15 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     int c = cluster_size_for(nt, std::max(1, ctx->sms - ctx->sm_reserve), g.max_m);
     const int w = cluster_warps(g.max_m);
     while (c >= 2 && w && tridiag_max_active_clusters(w, c, g.max_m) < nt) c /= 2;
-    if (c >= 2 && w) {
+    // the fewest, largest reductions: groups of more CTAs than a cluster can hold
+    const int gsz = ctx->groups_enabled
+                        ? group_size_for(nt, std::max(1, ctx->sms - ctx->sm_reserve), g.max_m) : 0;
+    if (gsz && (w == 12 || w == 16) && tridiag_group_blocks_per_sm(w, g.max_m) >= 1) {
+      g.gsize = gsz;
+      g.cfg = {false, w};
+      g.grid = nt;   // groups (= slots)
+      g.gsync_off = meta.take(sizeof(unsigned) * kGroupSyncWords * nt);
+    } else if (c >= 2 && w) {
       g.csize = c;
       g.cfg = {false, w};
       g.grid = nt;   // clusters (= slots)
@@ -508,7 +523,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   size_t counter2_off = 0;
   std::vector<char> in_tail(tri.size(), 0);
   if (ctx->overlap_enabled && !ctx->round_launches && gplans.size() == 1 && mode != MODE_EIGVALS &&
-      gplans[0].csize == 0 && !gplans[0].cfg.herm) {
+      gplans[0].csize == 0 && gplans[0].gsize == 0 && !gplans[0].cfg.herm) {
     GroupPlan& g = gplans[0];
     const int nt = (int)g.idx.size();
     const bool uniform = tri[g.idx.back()].m + 1 >= tri[g.idx.front()].m;
@@ -568,15 +583,25 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     (tri[t].col < 0 ? bis_a : in_tail[t] ? bis_m2 : bis_m).push_back((int)t);
   const size_t bt_off = meta.take(sizeof(BisectTask) * tri.size());
   // Bisection blocks, largest tasks first.  Runs of consecutive tasks (the minors of one
-  // matrix) of one small size m share a block, kBisectThreads / m of them at a time.
-  auto items_of = [&](const std::vector<int>& ts, std::vector<BisectItem>& items, int& mm) {
+  // matrix) of one small size m share a block, threads / m of them at a time.  A launch
+  // with few eigenvalues (fewer than 128 per SM) uses 64-lane blocks so that it spreads
+  // over more SMs (a single large matrix: the latency of a few-component call).
+  auto eig_count = [&](const std::vector<int>& ts) {
+    int64_t c = 0;
+    for (int t : ts) c += tri[t].m;
+    return c;
+  };
+  const int bis_threads_a = eig_count(bis_a) <= (int64_t)ctx->sms * 128 ? 64 : kBisectThreads;
+  const int bis_threads_m =
+      eig_count(bis_m) + eig_count(bis_m2) <= (int64_t)ctx->sms * 128 ? 64 : kBisectThreads;
+  auto items_of = [&](const std::vector<int>& ts, std::vector<BisectItem>& items, int& mm,
+                      int threads) {
     std::vector<int> order = ts;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tri[a].m > tri[b].m; });
     mm = 1;
     for (int t : order) mm = std::max(mm, tri[t].m);
     std::vector<BisectBlock> blocks;
-    plan_bisect_blocks(order, [&](int t) { return tri[t].m; }, kBisectThreads, kBisectMaxPack,
-                       blocks);
+    plan_bisect_blocks(order, [&](int t) { return tri[t].m; }, threads, kBisectMaxPack, blocks);
     for (const BisectBlock& b : blocks) {
       BisectItem it;
       it.task = b.task;
@@ -587,9 +612,9 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   };
   std::vector<BisectItem> items_a, items_m, items_m2;
   int mm_a = 1, mm_m = 1, mm_m2 = 1;
-  items_of(bis_a, items_a, mm_a);
-  items_of(bis_m, items_m, mm_m);
-  items_of(bis_m2, items_m2, mm_m2);
+  items_of(bis_a, items_a, mm_a, bis_threads_a);
+  items_of(bis_m, items_m, mm_m, bis_threads_m);
+  items_of(bis_m2, items_m2, mm_m2, bis_threads_m);
   const size_t bia_off = meta.take(sizeof(BisectItem) * std::max<size_t>(items_a.size(), 1));
   // the minors' items, then the tail minors' items, in one array (one launch over both
   // when the tail is not split off)
@@ -636,8 +661,9 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
       const double scale = (double)(ctx->budget - fixed) / (double)slots_total;
       for (auto& g : gplans) {
         if (g.cfg.smem) continue;
-        if (g.csize) {   // fewer slots than matrices: back to one CTA per matrix
+        if (g.csize || g.gsize) {   // fewer slots than matrices: back to one CTA per matrix
           g.csize = 0;
+          g.gsize = 0;
           g.cfg = tri_cfg(ctx, g.max_m);
           g.slot = tridiag_global_slot_doubles(g.max_m);
           g.grid = std::min<int>((int)g.idx.size(), ctx->sms * blocks_per_sm(ctx, g.cfg, g.max_m));
@@ -649,8 +675,11 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
         g.grid = ng;
       }
     }
-    for (auto& g : gplans)
+    for (auto& g : gplans) {
       if (!g.cfg.smem) g.work_off = dat.take(sizeof(double) * g.slot * g.grid);
+      if (g.gsize)
+        g.gw_off = dat.take(sizeof(double) * (size_t)(g.max_m + 96) * g.grid);
+    }
     // fewer slots than planned: the tail would not be a round of them, so the group
     // runs as one launch (both minor bisections then follow it)
     if (tail_at > 0 && gplans[0].grid != tail_grid_of) tail_at = 0;
@@ -784,7 +813,13 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
       }
       continue;
     }
-    if (g.csize) {
+    if (g.gsize) {
+      L.group = g.gsize;
+      L.gsync = (unsigned*)(ws + g.gsync_off);
+      L.gw = D(g.gw_off);
+      EEID_CK(launch_tridiag_group(g.cfg.warps, g.grid, g.gsize, L, stream),
+              "tridiag group launch");
+    } else if (g.csize) {
       EEID_CK(launch_tridiag_cluster(g.cfg.warps, g.grid, g.csize, L, stream),
               "tridiag cluster launch");
     } else {
@@ -817,7 +852,7 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
   if (!items_a.empty()) {
     EEID_CK(mark(EEID_PHASE_BISECT_A, 0, stream), "event");
     EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bia_off), (int)items_a.size(), mm_a,
-                          status_word, stream), "bisect(A) launch");
+                          status_word, stream, bis_threads_a), "bisect(A) launch");
     ctx->launches++;
     EEID_CK(mark(EEID_PHASE_BISECT_A, 1, stream), "event");
   }
@@ -833,13 +868,13 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     EEID_CK(mark(EEID_PHASE_BISECT_MINORS, 0, stream), "event");
     if (!items_m.empty()) {
       EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bim_off), (int)items_m.size(), mm_m,
-                            status_word, stream), "bisect(minors) launch");
+                            status_word, stream, bis_threads_m), "bisect(minors) launch");
       ctx->launches++;
     }
     if (tail_at > 0) EEID_CK(cudaStreamWaitEvent(stream, ctx->join_ev, 0), "join wait");
     if (!items_m2.empty()) {
       EEID_CK(launch_bisect(btd, (const BisectItem*)(ws + bim2_off), (int)items_m2.size(), mm_m2,
-                            status_word, stream), "bisect(tail minors) launch");
+                            status_word, stream, bis_threads_m), "bisect(tail minors) launch");
       ctx->launches++;
     }
     EEID_CK(mark(EEID_PHASE_BISECT_MINORS, 1, stream), "event");
@@ -961,6 +996,48 @@ void eeid_ctx_destroy(eeid_ctx* ctx) {
 int64_t eeid_launch_count(const eeid_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 int64_t eeid_vector_refs(const eeid_ctx* ctx) { return ctx ? ctx->vec_refs : 0; }
+
+eeid_status eeid_check_barrier_timeout(eeid_ctx* ctx, void* stream) {
+  eeid_status st = check_ctx(ctx);
+  if (st != EEID_OK) return st;
+  EEID_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  // a 2 x 2 matrix for a group of two CTAs, one of them never launched
+  const int m = 2;
+  const size_t slot = tridiag_global_slot_doubles(m);
+  const size_t off_task = 0, off_sync = 256, off_a = 512, off_de = off_a + 64,
+               off_gw = off_de + 64, off_slot = off_gw + sizeof(double) * (m + 96);
+  const size_t bytes = off_slot + sizeof(double) * slot;
+  char* buf = nullptr;
+  EEID_CK(cudaMalloc((void**)&buf, bytes), "cudaMalloc(barrier check)");
+  const double A[4] = {2.0, 0.0, 1.0, 3.0};
+  TridiagTask t{(const double*)(buf + off_a), 2, 2, -1, (double*)(buf + off_de),
+                (double*)(buf + off_de) + 2, -1, 0};
+  cudaError_t e = cudaMemsetAsync(buf, 0, bytes, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf + off_a, A, sizeof(A), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf + off_task, &t, sizeof(t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    TridiagLaunch L;
+    L.tasks = (const TridiagTask*)(buf + off_task);
+    L.ntasks = 1;
+    L.counter = nullptr;
+    L.work = (double*)(buf + off_slot);
+    L.work_stride = (int64_t)slot;
+    L.max_m = m;
+    L.status = ctx->d_status + status_slot(ctx, s, true);
+    L.group = 2;
+    L.gsync = (unsigned*)(buf + off_sync);
+    L.gw = (double*)(buf + off_gw);
+    e = launch_tridiag_group_short(L, s);
+    if (e == cudaSuccess) ctx->launches++;
+  }
+  // the host copies above read stack memory: wait for them (and the launch) before return
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  EEID_CK(e, "barrier check launch");
+  EEID_CK(e2, "barrier check");
+  return EEID_OK;
+}
 
 eeid_status eeid_tune_tridiag(eeid_ctx* ctx, int m_lo, int m_hi, int path, int warps) {
   eeid_status st = check_ctx(ctx);
@@ -1143,10 +1220,12 @@ eeid_status set_sm_reserve(eeid_ctx* ctx, int sms) {
 
 extern "C" {
 
-eeid_status eeid_set_clusters(eeid_ctx* ctx, int enable) {
+eeid_status eeid_set_clusters(eeid_ctx* ctx, int mode) {
   eeid_status st = check_ctx(ctx);
   if (st != EEID_OK) return st;
-  ctx->clusters_enabled = enable != 0;   // part of the graph key: no graph goes stale
+  if (mode < 0 || mode > 2) return fail(EEID_ERR_INVALID, "cluster mode %d (0, 1 or 2)", mode);
+  ctx->clusters_enabled = mode != 0;   // part of the graph key: no graph goes stale
+  ctx->groups_enabled = mode == 2;
   return EEID_OK;
 }
 
@@ -1209,6 +1288,8 @@ eeid_status eeid_sync(eeid_ctx* ctx, void* stream) {
   EEID_CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   const unsigned bits = ctx->h_status[slot];
   if (bits & ST_BAD_TASK) return fail(EEID_ERR_INVALID, "a kernel met a task beyond its size limit");
+  if (bits & ST_TIMEOUT)
+    return fail(EEID_ERR_TIMEOUT, "a cooperative reduction's barrier wait ran out; its outputs are invalid");
   if (bits & ST_DEGENERATE)
     return fail(EEID_WARN_DEGENERATE, "equal eigenvalues of A: Eq. 1 is 0/0; rows set to NaN");
   if (bits & ST_SMALL_GAP)
@@ -1296,7 +1377,7 @@ eeid_status eeid_components_batched(eeid_ctx* ctx, const eeid_problem* in, int64
   const int slot = status_slot(ctx, s, true);
   std::string key = std::to_string(slot) + ":" + batch_key(probs, ctx->timing, ctx->rules_version,
                               (ctx->overlap_enabled ? 1 : 0) | (ctx->round_launches ? 2 : 0) |
-                                  (ctx->clusters_enabled ? 4 : 0));
+                                  (ctx->clusters_enabled ? 4 : 0) | (ctx->groups_enabled ? 8 : 0));
   for (auto& g : ctx->graphs) {
     if (g.key == key) {
       g.last_use = ++ctx->graph_clock;

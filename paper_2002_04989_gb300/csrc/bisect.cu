@@ -371,14 +371,15 @@ static std::atomic<uint64_t> g_bisect_limit_set{0};
 cudaError_t preload_bisect() { return raise_smem_limit_once((const void*)k_bisect, g_bisect_limit_set); }
 
 cudaError_t launch_bisect(const BisectTask* tasks, const BisectItem* items, int nitems, int max_m,
-                          unsigned* status, cudaStream_t s) {
+                          unsigned* status, cudaStream_t s, int threads) {
+  if (threads < 32 || threads > kBisectThreads || threads % 32) return cudaErrorInvalidValue;
   if (nitems <= 0) return cudaSuccess;
   // room for one task of max_m rows or for packed tasks of up to kBisectThreads rows
   const size_t rows = (size_t)(max_m > kBisectThreads ? max_m : kBisectThreads);
   const size_t smem = rows * (sizeof(double2) + sizeof(float4));
   cudaError_t e = raise_smem_limit_once((const void*)k_bisect, g_bisect_limit_set);
   if (e != cudaSuccess) return e;
-  k_bisect<<<nitems, kBisectThreads, smem, s>>>(tasks, items, status);
+  k_bisect<<<nitems, threads, smem, s>>>(tasks, items, status);
   return cudaGetLastError();
 }
 

@@ -86,6 +86,19 @@ inline int cluster_size_for(int nt, int sms, int max_m, int min_m = kClusterMinM
   return c >= 2 ? c : 0;
 }
 
+// Group plan (the group variant): when even clusters of 16 would leave most SMs idle (a
+// call with a handful of large reductions, e.g. one component of a large A: A and one
+// minor), G = sms / nt CTAs reduce each matrix, resident together through a cooperative
+// launch, meeting at global-memory barriers.  0 = no group plan (G would not exceed the
+// cluster limit, or the matrices are below min_m, where two global barriers a step cost
+// more than the split saves).
+constexpr int kGroupMinM = 1536;
+inline int group_size_for(int nt, int sms, int max_m, int min_m = kGroupMinM) {
+  if (nt < 1 || max_m < min_m) return 0;
+  const int g = sms / nt;
+  return g > kClusterMaxCtas ? g : 0;
+}
+
 // Efficiency of a reduction split over a cluster of c CTAs, relative to one CTA, for an
 // m x m matrix.  The phases outside the fused pass (column update, reflector, the sums of
 // the partials, w) run redundantly in every CTA of a cluster and do not shrink with c;

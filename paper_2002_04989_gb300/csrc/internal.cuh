@@ -37,6 +37,7 @@ enum : unsigned {
   ST_SMALL_GAP = 2u,       // min relative gap < 1e-4
   ST_BRACKET_FALLBACK = 4u,// an interlacing bracket failed its Sturm check (info)
   ST_BAD_TASK = 8u,        // a kernel met a task it cannot run (size limit)
+  ST_TIMEOUT = 16u,        // a bounded wait of a cooperative reduction ran out (no result)
 };
 
 // ---------------------------------------------------------------- K-a tridiag
@@ -73,7 +74,14 @@ struct TridiagLaunch {
   int64_t work_stride;       // doubles per CTA slot (matrix + partials)
   int max_m;                 // largest m among tasks (sizes the per-CTA layout)
   unsigned* status;
+  // Group variant only: `group` CTAs reduce task (blockIdx.x / group) together.  gsync:
+  // per group kGroupSyncWords words (arrival counter, abort flag), zero at launch; gw: per
+  // group a vector of VM doubles through which the CTAs exchange w.
+  int group = 0;
+  unsigned* gsync = nullptr;
+  double* gw = nullptr;
 };
+constexpr int kGroupSyncWords = 8;
 
 size_t tridiag_global_slot_doubles(int max_m);
 size_t tridiag_smem_bytes(bool smem_path, int max_m, int warps);
@@ -103,8 +111,11 @@ struct BisectItem {
 };
 constexpr int kBisectThreads = 256;
 constexpr int kBisectMaxPack = 64;   // packed tasks per block (so m >= 4 when packing)
+// threads: block size (a multiple of 32, at most kBisectThreads; the items were planned for
+// it).  Launches with few eigenvalues use small blocks so that they reach more SMs.
 cudaError_t launch_bisect(const BisectTask* tasks, const BisectItem* items, int nitems,
-                          int max_m, unsigned* status, cudaStream_t s);
+                          int max_m, unsigned* status, cudaStream_t s,
+                          int threads = kBisectThreads);
 
 // ---------------------------------------------------------------- K-c identity
 // D_i = prod_{k != i} |lam_i - lam_k| for the requested eigen-indices i = rows[r] of

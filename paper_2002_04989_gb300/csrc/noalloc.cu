@@ -44,7 +44,8 @@ static_assert(sizeof(TridiagTask) <= 64, "descriptor layout");
 static_assert(sizeof(BisectTask) <= 64, "descriptor layout");
 static_assert(kOffItems + 4 * sizeof(BisectItem) <= kOffStatus, "descriptor layout");
 static_assert(ST_DEGENERATE == EEID_DEV_DEGENERATE && ST_SMALL_GAP == EEID_DEV_SMALL_GAP &&
-                  ST_BRACKET_FALLBACK == EEID_DEV_BRACKET_FALLBACK && ST_BAD_TASK == EEID_DEV_BAD_TASK,
+                  ST_BRACKET_FALLBACK == EEID_DEV_BRACKET_FALLBACK && ST_BAD_TASK == EEID_DEV_BAD_TASK &&
+                  ST_TIMEOUT == EEID_DEV_TIMEOUT,
               "device status bits of the header");
 
 // The scratch: 2.2 MB held by every GPU that loads the library, for the life of

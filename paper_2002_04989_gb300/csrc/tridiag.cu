@@ -251,6 +251,57 @@ __device__ __forceinline__ void block_or_cluster_sync() {
   }
 }
 
+// Barrier of a group of G CTAs that reduce one matrix together (the group variant), in
+// global memory: each arrival adds 1 to the group's counter, and the k-th barrier is
+// passed once the counter reaches k*G (the counter only grows within a launch, so there is
+// no reset to race with).  Writes before the barrier are made visible by the fences on
+// both sides (the pattern of a grid-wide cooperative barrier).  The wait is bounded: after
+// kGroupWaitNs of the global timer (or kGroupSpinLimit polls, whichever comes first) the
+// CTA raises the group's abort flag and ST_TIMEOUT; a CTA that sees the flag stops
+// waiting too.  Returns false when the group gave up (the caller then returns without
+// writing its outputs).
+constexpr unsigned long long kGroupWaitNs = 1000000000ull;   // 1 s
+constexpr unsigned kGroupSpinLimit = 1u << 24;               // >= 1 s at >= 64 ns a poll
+struct GroupSync {
+  unsigned* cnt;
+  unsigned* abort_flag;
+  unsigned target;
+  unsigned G;
+};
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __noinline__ bool group_sync(GroupSync& gs, unsigned* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    gs.target += gs.G;
+    __threadfence();
+    atomicAdd(gs.cnt, 1u);
+    const volatile unsigned* c = gs.cnt;
+    const volatile unsigned* ab = gs.abort_flag;
+    const unsigned long long t0 = global_ns();
+    unsigned polls = 0;
+    while (*c < gs.target) {
+      if (*ab) { ok = 0; break; }
+      if (++polls > kGroupSpinLimit || global_ns() - t0 > kGroupWaitNs) {
+        atomicExch(gs.abort_flag, 1u);
+        atomicOr(status, (unsigned)ST_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // Minimum resident CTAs per SM the register allocation must allow.
 // HI: the high-occupancy build of the global-slot variant (at most 80 registers a thread:
 // three 8-warp or six 4-warp CTAs per SM, a little register spilling), for small matrices
@@ -268,7 +319,11 @@ struct MinBlocks {
 // the same tile order and writes them into every CTA's shared copy of w (distributed
 // shared memory).  The serial phases (A-C, gamma, F) run redundantly in every CTA on
 // identical data.  So the results are bitwise those of the one-CTA global variant.
-template <bool SMEM, int W, bool CL = false, bool HI = false>
+// GR = true: the group variant (global-slot path only).  P.group CTAs, resident together
+// (cooperative launch), reduce one matrix exactly as a cluster does, but exchange w through
+// a vector in global memory and meet at global-memory barriers (group_sync), so a group
+// can span any number of SMs.  Each group takes one task (blockIdx.x / P.group).
+template <bool SMEM, int W, bool CL = false, bool HI = false, bool GR = false>
 __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tridiag(TridiagLaunch P) {
   extern __shared__ __align__(16) double sm[];
   constexpr int NT = W * 32;
@@ -280,6 +335,18 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
     crank = (int)cluster.block_rank();
     csize = (int)cluster.num_blocks();
   }
+  GroupSync gs{nullptr, nullptr, 0u, 1u};
+  double* gw = nullptr;
+  if constexpr (GR) {
+    csize = P.group;
+    crank = (int)blockIdx.x % csize;
+    const int gid = (int)blockIdx.x / csize;
+    gs.cnt = P.gsync + (size_t)gid * kGroupSyncWords;
+    gs.abort_flag = gs.cnt + 1;
+    gs.G = (unsigned)csize;
+    gw = P.gw + (size_t)gid * make_layout(false, P.max_m).VM;
+  }
+  int rounds_done = 0;
   const int gwarp = crank * W + warp, GW = csize * W;   // warp index within the cluster
   const Layout Ly = make_layout(SMEM, P.max_m);
   const int64_t ld = Ly.ld;
@@ -311,7 +378,10 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
   __shared__ int s_task;
 
   for (;;) {
-    if constexpr (CL) {
+    if constexpr (GR) {
+      // one task per group, no counter
+      s_task = rounds_done++ == 0 ? (int)blockIdx.x / csize : P.ntasks;
+    } else if constexpr (CL) {
       // rank 0 takes the cluster's next task and hands it to every CTA
       cg::cluster_group cluster = cg::this_cluster();
       if (crank == 0 && tid == 0) {
@@ -327,6 +397,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
     if constexpr (CL) cg::this_cluster().sync();
     else __syncthreads();
     if (t >= P.ntasks) break;
+    (void)rounds_done;
     const TridiagTask task = P.tasks[t];
     const int skip = task.skip;
     const int m = task.n - (skip >= 0 ? 1 : 0);
@@ -383,7 +454,11 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
         }
       }
     }
-    block_or_cluster_sync<CL>();
+    if constexpr (GR) {
+      if (!group_sync(gs, P.status)) return;
+    } else {
+      block_or_cluster_sync<CL>();
+    }
 
     for (int k = 0; k + 2 < m; ++k) {
       const int base = k + 1;
@@ -477,7 +552,11 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
           if (++J > I) { ++I; J = 0; }
         }
       }
-      block_or_cluster_sync<CL>();
+      if constexpr (GR) {
+        if (!group_sync(gs, P.status)) return;
+      } else {
+        block_or_cluster_sync<CL>();
+      }
       // ---- Phase E: p = tau * (row partials + column partials); gamma = tau/2 p.v
       // (cluster variant: each CTA sums every csize-th run of NT elements and writes
       // them into the w of every CTA of the cluster)
@@ -496,12 +575,23 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
         if constexpr (CL) {
           cg::cluster_group cluster = cg::this_cluster();
           for (int r2 = 0; r2 < csize; ++r2) cluster.map_shared_rank(wC, r2)[i] = p * tau;
+        } else if constexpr (GR) {
+          gw[i] = p * tau;
         } else {
           wC[i] = p * tau;
         }
       }
-      if constexpr (CL) cg::this_cluster().sync();
-      else __syncthreads();
+      if constexpr (CL) {
+        cg::this_cluster().sync();
+      } else if constexpr (GR) {
+        // every CTA takes the whole p tau from the group's vector (read at L2: other SMs
+        // wrote it)
+        if (!group_sync(gs, P.status)) return;
+        for (int i = base + tid; i < m; i += NT) wC[i] = __ldcg(gw + i);
+        __syncthreads();
+      } else {
+        __syncthreads();
+      }
       if (warp == 0) {
         const double dot = warp_dot(wC, vC, base, m, lane);
         if (lane == 0) scal[3] = 0.5 * tau * dot;
@@ -665,6 +755,77 @@ cudaError_t launch_tridiag_cluster(int warps, int nclusters, int csize, const Tr
   return cudaErrorInvalidValue;
 }
 
+// ---- group variant: `group` CTAs per matrix, resident together (cooperative launch)
+
+template <int W>
+std::atomic<uint64_t>& group_limit_set() {
+  static std::atomic<uint64_t> done{0};
+  return done;
+}
+
+template <int W>
+static cudaError_t launch_group_one(int nctas, const TridiagLaunch& L, cudaStream_t s) {
+  const void* kern = (const void*)k_tridiag<false, W, false, false, true>;
+  cudaError_t e = raise_smem_limit_once(kern, group_limit_set<W>());
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nctas, 1, 1);
+  cfg.blockDim = dim3(W * 32, 1, 1);
+  cfg.dynamicSmemBytes = tridiag_smem_bytes(false, L.max_m, W);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident at once, or no launch
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k_tridiag<false, W, false, false, true>, L);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Launch ngroups groups of `group` CTAs (L.group must equal group; L.ntasks <= ngroups).
+cudaError_t launch_tridiag_group(int warps, int ngroups, int group, const TridiagLaunch& L,
+                                 cudaStream_t s) {
+  if (L.group != group || !L.gsync || !L.gw || group < 1) return cudaErrorInvalidValue;
+  switch (warps) {
+    case 12: return launch_group_one<12>(ngroups * group, L, s);
+    case 16: return launch_group_one<16>(ngroups * group, L, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Self-test of the bounded barrier: one group of L.group >= 2 CTAs of which only
+// L.group - 1 are launched, so the group's first barrier never fills and every launched
+// CTA gives up after the wait limit with ST_TIMEOUT (L.ntasks = 1).
+cudaError_t launch_tridiag_group_short(const TridiagLaunch& L, cudaStream_t s) {
+  if (L.group < 2 || !L.gsync || !L.gw || L.ntasks != 1) return cudaErrorInvalidValue;
+  return launch_group_one<16>(L.group - 1, L, s);
+}
+
+// CTAs of the group variant that fit on one SM for matrices up to max_m (0 on error).
+int tridiag_group_blocks_per_sm(int warps, int max_m) {
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  const size_t smem = tridiag_smem_bytes(false, max_m, warps);
+  if (warps == 12) {
+    e = raise_smem_limit_once((const void*)k_tridiag<false, 12, false, false, true>,
+                              group_limit_set<12>());
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tridiag<false, 12, false, false, true>,
+                                                        384, smem);
+  } else if (warps == 16) {
+    e = raise_smem_limit_once((const void*)k_tridiag<false, 16, false, false, true>,
+                              group_limit_set<16>());
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tridiag<false, 16, false, false, true>,
+                                                        512, smem);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
 // Clusters of csize CTAs of the `warps`-warp cluster variant that fit on the device at
 // once for matrices up to max_m (0 if none, or on an error).
 int tridiag_max_active_clusters(int warps, int csize, int max_m) {
@@ -704,6 +865,12 @@ cudaError_t preload_tridiag() {
   if (e == cudaSuccess) e = prepare_cluster_kernel<8>();
   if (e == cudaSuccess) e = prepare_cluster_kernel<12>();
   if (e == cudaSuccess) e = prepare_cluster_kernel<16>();
+  if (e == cudaSuccess)
+    e = raise_smem_limit_once((const void*)k_tridiag<false, 12, false, false, true>,
+                              group_limit_set<12>());
+  if (e == cudaSuccess)
+    e = raise_smem_limit_once((const void*)k_tridiag<false, 16, false, false, true>,
+                              group_limit_set<16>());
   return e;
 }
 

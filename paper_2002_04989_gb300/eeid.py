@@ -31,6 +31,7 @@ EEID_DEV_DEGENERATE = 1
 EEID_DEV_SMALL_GAP = 2
 EEID_DEV_BRACKET_FALLBACK = 4
 EEID_DEV_BAD_TASK = 8
+EEID_DEV_TIMEOUT = 16
 
 _lock = threading.Lock()
 _lib = None
@@ -93,6 +94,7 @@ SIGNATURES = {
     "eeid_set_graphs": ([_vp, ctypes.c_int], ctypes.c_int),
     "eeid_set_overlap": ([_vp, ctypes.c_int], ctypes.c_int),
     "eeid_set_clusters": ([_vp, ctypes.c_int], ctypes.c_int),
+    "eeid_check_barrier_timeout": ([_vp, _vp], ctypes.c_int),
     "eeid_server_create": ([ctypes.c_int, ctypes.POINTER(EeidServerOpts), ctypes.POINTER(_vp)],
                            ctypes.c_int),
     "eeid_server_destroy": ([_vp], None),
@@ -375,8 +377,16 @@ class Context:
     def eeid_set_overlap(self, enable: bool = True) -> int:
         return _check(self.lib.eeid_set_overlap(self.handle, 1 if enable else 0), False)
 
-    def eeid_set_clusters(self, enable: bool = True) -> int:
-        return _check(self.lib.eeid_set_clusters(self.handle, 1 if enable else 0), False)
+    def eeid_set_clusters(self, mode=2) -> int:
+        """False/0: off; True/1: the cluster plan only; 2 (default): clusters plus the group
+        plan."""
+        mode = int(mode)
+        if mode not in (0, 1, 2):
+            raise ValueError(f"cluster mode {mode} (0, 1 or 2)")
+        return _check(self.lib.eeid_set_clusters(self.handle, mode), False)
+
+    def eeid_check_barrier_timeout(self, stream=None) -> int:
+        return _check(self.lib.eeid_check_barrier_timeout(self.handle, _stream(stream)), False)
 
     def launch_count(self) -> int:
         return int(self.lib.eeid_launch_count(self.handle))

@@ -1,8 +1,10 @@
 """The cluster plan (latency mode, eeid_set_clusters): a call with few large reductions
 (a single component, a few columns, the eigenvalues of one A) reduces each matrix on a
-thread-block cluster of up to 16 CTAs.  The results must be bitwise those of the
+thread-block cluster of up to 16 CTAs, and with mode 2 the fewest largest ones on a
+cooperative group of sms / nt > 16 CTAs.  The results must be bitwise those of the
 one-CTA plan, and match the planted closed form Q o Q within the library's bar; the
-single-component call (the paper's Table 1 task) must also be faster."""
+single-component call (the paper's Table 1 task) must also be faster.  The group plan's
+bounded barrier is checked by its self-test (a group with a CTA missing)."""
 import time
 
 import numpy as np
@@ -28,7 +30,7 @@ def ctx(torch_cuda):
     from paper_2002_04989_gb300 import eeid
     c = eeid.Context(0)
     yield c
-    c.eeid_set_clusters(True)
+    c.eeid_set_clusters(2)
     c.close()
 
 
@@ -68,6 +70,49 @@ def test_cluster_eigvals_and_minors_bitwise(torch_cuda, ctx):
     assert np.array_equal(out[True][1], out[False][1])
 
 
+@pytest.mark.parametrize("n,cols", [(1600, [7]), (2100, [0, 1050, 2099])])
+def test_group_plan_bitwise_and_closed_form(torch_cuda, ctx, n, cols):
+    """Two or four reductions of m >= 1536: mode 2 runs each on 76 or 38 CTAs that meet at
+    global-memory barriers; same bits as the one-CTA plan and the cluster plan."""
+    p = inputs.planted(n, 1700 + n, -1.0, 1.0, 1e-4)
+    A = torch_cuda.from_numpy(p.A).cuda()
+    rows = np.unique(np.r_[0, n // 3, n - 1])
+    got_g, lam_g = run(torch_cuda, ctx, A, rows, cols, 2)
+    got_c, lam_c = run(torch_cuda, ctx, A, rows, cols, 1)
+    got_p, lam_p = run(torch_cuda, ctx, A, rows, cols, 0)
+    assert np.array_equal(got_g, got_p) and np.array_equal(lam_g, lam_p)
+    assert np.array_equal(got_c, got_p)
+    ref = (p.Q * p.Q).T[np.ix_(rows, cols)]
+    assert np.max(np.abs(got_g - ref)) <= TOL_VSQ
+    assert np.max(np.abs(lam_g - p.lam)) <= 1e-12
+
+
+def test_group_plan_eigvals_bitwise(torch_cuda, ctx):
+    """The eigenvalues of one n = 3000 matrix: a single group of every SM."""
+    A = torch_cuda.from_numpy(inputs.goe(3000, 78)).cuda()
+    out = {}
+    for mode in (2, 0):
+        ctx.eeid_set_clusters(mode)
+        out[mode] = ctx.eeid_eigvals(A).cpu().numpy()
+        assert ctx.eeid_sync() >= 0
+    assert np.array_equal(out[2], out[0])
+
+
+def test_group_barrier_timeout_reported(torch_cuda, ctx):
+    """A group whose partner CTA never arrives gives up after the wait limit: eeid_sync
+    reports EEID_ERR_TIMEOUT, and the context keeps working afterwards."""
+    from paper_2002_04989_gb300 import eeid
+    ctx.eeid_check_barrier_timeout()
+    with pytest.raises(eeid.EeidError) as ei:
+        ctx.eeid_sync()
+    assert ei.value.status == eeid.EEID_ERR_TIMEOUT
+    assert ctx.eeid_sync() == 0          # the word was cleared by the read
+    p = inputs.planted(300, 31, -1.0, 1.0, 1e-4)
+    out = ctx.eeid_components(torch_cuda.from_numpy(p.A).cuda(), cols=[4])
+    assert ctx.eeid_sync() == 0
+    assert np.max(np.abs(out.cpu().numpy()[:, 0] - p.Q[4] ** 2)) <= TOL_VSQ
+
+
 def test_single_component_n4002(torch_cuda, ctx):
     """One component of an n = 4002 planted matrix (the largest Table 1 size the
     library's n <= 4096 limit allows near 4002): against Q o Q, and faster than the
@@ -77,7 +122,7 @@ def test_single_component_n4002(torch_cuda, ctx):
     A = torch.from_numpy(p.A).cuda()
     i, j = 1234, 2001
     times = {}
-    for cl in (True, False):
+    for cl in (2, True, False):
         ctx.eeid_set_clusters(cl)
         ctx.eeid_components(A, rows=[i], cols=[j])     # warm-up (workspace sizing)
         ctx.eeid_sync()
@@ -87,9 +132,10 @@ def test_single_component_n4002(torch_cuda, ctx):
         times[cl] = time.perf_counter() - t0
         v = float(out.cpu().numpy()[0, 0])
         assert abs(v - p.Q[j, i] ** 2) <= TOL_VSQ, (cl, v, p.Q[j, i] ** 2)
-    print(f"n=4002 one component: cluster plan {times[True]:.3f} s, one CTA per matrix "
-          f"{times[False]:.3f} s")
+    print(f"n=4002 one component: group plan {times[2]:.3f} s, cluster plan "
+          f"{times[True]:.3f} s, one CTA per matrix {times[False]:.3f} s")
     assert times[True] < 0.5 * times[False]
+    assert times[2] < 0.7 * times[True]
 
 
 def test_cluster_rounds_bitwise_and_closed_form(torch_cuda, ctx):

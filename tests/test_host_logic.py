@@ -30,6 +30,8 @@ int main(int argc, char** argv) {
     printf("%d %d %d %d\n", p.hybrid ? 1 : 0, p.bulk_grid, p.tail_at, p.tail_grid);
   } else if (!strcmp(argv[1], "cluster")) {
     printf("%d\n", cluster_size_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])));
+  } else if (!strcmp(argv[1], "group")) {
+    printf("%d\n", group_size_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])));
   } else if (!strcmp(argv[1], "crounds")) {
     // nt sms m a2 a4 a8 a16 t_single
     int act[4] = {atoi(argv[5]), atoi(argv[6]), atoi(argv[7]), atoi(argv[8])};
@@ -197,6 +199,26 @@ def test_cluster_plan(driver):
             assert k == 16 or nt * 2 * k > sms       # the largest such power of two
         else:
             assert 2 * nt > sms
+
+
+def test_group_plan(driver):
+    g = lambda nt, sms=152, m=4001: int(driver("group", nt, sms, m)[0])
+    # one component of n = 4002 (A and one minor): two groups of 76 CTAs
+    assert g(2) == 76
+    # the eigenvalues of one large A: every SM
+    assert g(1) == 152
+    # as long as a group exceeds the cluster limit of 16
+    assert g(3) == 50
+    assert g(8) == 19 and g(9) == 0 and g(10) == 0
+    # below the size floor (two global barriers a step would cost more than they save)
+    assert g(2, m=1535) == 0 and g(2, m=1536) == 76
+    rng = np.random.default_rng(6)
+    for _ in range(200):
+        nt, sms = int(rng.integers(1, 40)), int(rng.integers(2, 200))
+        k = g(nt, sms)
+        assert k == (sms // nt if sms // nt > 16 else 0)
+        if k:
+            assert nt * k <= sms
 
 
 def test_cluster_rounds(driver):
