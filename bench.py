@@ -679,15 +679,18 @@ def run_profile_case(case: str) -> int:
     k_identity launches are the ones captured for those kernels); batch256 = the
     matrices of the uneven batch with n in (192, 256] (316 of them) in one batched call
     with the autotuned variants, graphs off, called twice; single2002 = one component of
-    a planted n = 2002 matrix (the cluster plan), called twice; herm512 = a complex
+    a planted n = 2002 matrix (the group plan: two groups of 76 CTAs), called twice;
+    cluster2002 = the same on the cluster plan (two clusters of 16); herm512 = a complex
     Hermitian n = 512 matrix with 151 columns, called twice."""
     import numpy as np
     import torch
 
     from paper_2002_04989_gb300 import eeid, inputs
     ctx = eeid.Context(0)
-    if case == "single2002":
-        # one component of a planted n = 2002 matrix: A and one minor, two clusters of 16
+    if case in ("single2002", "cluster2002"):
+        # one component of a planted n = 2002 matrix: A and one minor, two groups of 76
+        # CTAs (or two clusters of 16)
+        ctx.eeid_set_clusters(2 if case == "single2002" else 1)
         pl = inputs.planted(2002, 2002, -1.0, 1.0, 1e-4)
         A = torch.from_numpy(pl.A).cuda()
         for _ in range(2):
@@ -754,7 +757,7 @@ def main(argv=None):
     ap.add_argument("--serving-rates", default="0.5,1,2",
                     help="serving: comma-separated Poisson arrival rates (requests/s)")
     ap.add_argument("--profile-case", choices=("tridiag152", "tridiag304", "batch256", "single2002",
-                                               "herm512"), default=None,
+                                               "cluster2002", "herm512"), default=None,
                     help="run only a small case for an ncu capture and exit: tridiag152 / "
                          "tridiag304 = A plus the first 151 / 303 minors of the planted "
                          "n=1024 matrix (one / two CTAs per SM), called twice")

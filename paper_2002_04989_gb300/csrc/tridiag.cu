@@ -29,6 +29,7 @@
 //   SMEM = false  it lives in a per-CTA slot of global memory (L2-resident for
 //                 small m), tiles are staged through a per-warp shared buffer.
 #include "internal.cuh"
+#include "tile_split.h"
 
 #include <cooperative_groups.h>
 #include <cstdio>
@@ -215,10 +216,6 @@ __device__ __forceinline__ void diag_tile(double* S, int64_t ld, int m, int R0, 
   __syncwarp();
 }
 
-// Balanced split of the nb(nb+1)/2 lower-triangle tiles of one step over the W
-// warps (global-slot variant): warp w takes the tiles t in [start(w), start(w+1)) of
-// the row-major tile order t = I(I+1)/2 + J.
-__device__ __forceinline__ int tile_start(int w, int T, int W) { return (int)(((int64_t)w * T) / W); }
 
 __device__ __forceinline__ int snake_owner(int I, int W) {
   const int q = I / W, r = I % W;
@@ -255,7 +252,8 @@ __device__ __forceinline__ void block_or_cluster_sync() {
 // global memory: each arrival adds 1 to the group's counter, and the k-th barrier is
 // passed once the counter reaches k*G (the counter only grows within a launch, so there is
 // no reset to race with).  Writes before the barrier are made visible by the fences on
-// both sides (the pattern of a grid-wide cooperative barrier).  The wait is bounded: after
+// both sides (release before the arrival, acquire after the wait; the CTA barriers order
+// the other threads' accesses around thread 0's).  The wait is bounded: after
 // kGroupWaitNs of the global timer (or kGroupSpinLimit polls, whichever comes first) the
 // CTA raises the group's abort flag and ST_TIMEOUT; a CTA that sees the flag stops
 // waiting too.  Returns false when the group gave up (the caller then returns without
@@ -279,7 +277,7 @@ __device__ __noinline__ bool group_sync(GroupSync& gs, unsigned* status) {
   if (threadIdx.x == 0) {
     int ok = 1;
     gs.target += gs.G;
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");   // release
     atomicAdd(gs.cnt, 1u);
     const volatile unsigned* c = gs.cnt;
     const volatile unsigned* ab = gs.abort_flag;
@@ -295,12 +293,15 @@ __device__ __noinline__ bool group_sync(GroupSync& gs, unsigned* status) {
       }
       __nanosleep(64);
     }
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");   // acquire
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
 }
+
+// Loads in flight per thread while the split variants stage Phase E's partials.
+constexpr int kEStage = 8;
 
 // Minimum resident CTAs per SM the register allocation must allow.
 // HI: the high-occupancy build of the global-slot variant (at most 80 registers a thread:
@@ -465,16 +466,30 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
       const bool upd = (k > 0);
       // ---- Phase A: apply update k-1 to column k; x = column below the diagonal.
       const double vPk = upd ? vP[k] : 0.0, wPk = upd ? wP[k] : 0.0;
-      for (int i = k + tid; i < m; i += NT) {
-        double a = S[(size_t)i * ld + k];
-        if (upd) a = fma(-vP[i], wPk, fma(-wP[i], vPk, a));
-        if (i == k) {
-          if (crank == 0) dout[k] = a;
-        } else if (i == k + 1) {
-          scal[0] = a;       // alpha
-          vC[i] = 1.0;
-        } else {
-          vC[i] = a;
+      // split variants (short steps): the column's loads are issued four at a time, so a
+      // long column costs a few memory latencies, not one per element
+      constexpr int QA = (CL || GR) ? 4 : 1;
+      for (int i0 = k + tid; i0 < m; i0 += QA * NT) {
+        double col[QA];
+#pragma unroll
+        for (int q = 0; q < QA; ++q) {
+          const int i = i0 + q * NT;
+          col[q] = i < m ? S[(size_t)i * ld + k] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < QA; ++q) {
+          const int i = i0 + q * NT;
+          if (i >= m) break;
+          double a = col[q];
+          if (upd) a = fma(-vP[i], wPk, fma(-wP[i], vPk, a));
+          if (i == k) {
+            if (crank == 0) dout[k] = a;
+          } else if (i == k + 1) {
+            scal[0] = a;       // alpha
+            vC[i] = 1.0;
+          } else {
+            vC[i] = a;
+          }
         }
       }
       __syncthreads();
@@ -529,8 +544,7 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
       } else {
         // contiguous, balanced range of tiles per warp; each tile leaves its column
         // partial in tpart and its row partial in upart (both indexed by tile)
-        const int T = nb * (nb + 1) / 2;
-        const int t0 = tile_start(gwarp, T, GW), t1 = tile_start(gwarp + 1, T, GW);
+        const int t0 = tile_start(gwarp, nb, GW), t1 = tile_start(gwarp + 1, nb, GW);
         int I = 0;
         while ((I + 1) * (I + 2) / 2 <= t0) ++I;
         int J = t0 - I * (I + 1) / 2;
@@ -557,21 +571,12 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
       } else {
         block_or_cluster_sync<CL>();
       }
-      // ---- Phase E: p = tau * (row partials + column partials); gamma = tau/2 p.v
-      // (cluster variant: each CTA sums every csize-th run of NT elements and writes
-      // them into the w of every CTA of the cluster)
-      for (int i = base + crank * NT + tid; i < m; i += GW * 32) {
-        const int r = i - base, I = r >> 5, l = r & 31;
-        double p;
-        if (SMEM) {
-          p = upart[I * 32 + l];
-        } else {
-          // row partials of the tiles of block-row I, in tile order
-          const double* up = upart + (size_t)I * nbmax * 32 + l;
-          p = up[0];
-          for (int J = 1; J <= I; ++J) p += up[(size_t)J * 32];
-        }
-        for (int I2 = I; I2 < nb; ++I2) p += tpart[((size_t)I2 * nbmax + I) * 32 + l];
+      // ---- Phase E: p = tau * (row partials + column partials); gamma = tau/2 p.v.
+      // Element i (block-row I, lane l) sums the row partials of the tiles of block-row I,
+      // then the column partials of block-column I, each in tile order: the same order in
+      // every variant.  The result goes to w (cluster: to the w of every CTA of the
+      // cluster; group: to the group's vector in global memory).
+      auto put_p = [&](int i, double p) {
         if constexpr (CL) {
           cg::cluster_group cluster = cg::this_cluster();
           for (int r2 = 0; r2 < csize; ++r2) cluster.map_shared_rank(wC, r2)[i] = p * tau;
@@ -579,6 +584,59 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
           gw[i] = p * tau;
         } else {
           wC[i] = p * tau;
+        }
+      };
+      // Split variants (short steps): the block-rows I = crank, crank + csize, ... are
+      // taken RB at a time; all threads first stage the nb + 1 partials of each of their
+      // elements in shared memory (the tile scratch, idle now), kEStage loads in flight a
+      // thread, and one warp per block-row then adds them from there.
+      const int e_per = (nb + 1) * 32;
+      const int e_rb = (W * kTile * kTilePad) / e_per;
+      if ((CL || GR) && !SMEM && e_rb >= 1) {
+        double* stg = scal + 8;
+        const int RB = e_rb < W ? e_rb : W;
+        for (int I0 = crank; I0 < nb; I0 += RB * csize) {
+          const int left = (nb - 1 - I0) / csize + 1;   // block-rows I0, I0 + csize, ... < nb
+          const int nrow = left < RB ? left : RB;
+          const int total = nrow * e_per;
+          for (int x0 = tid; x0 < total; x0 += kEStage * NT) {
+            double v[kEStage];
+#pragma unroll
+            for (int u = 0; u < kEStage; ++u) {
+              const int x = x0 + u * NT;
+              const int bq = x / e_per, r = x - bq * e_per, q = r >> 5, l = r & 31;
+              const int I = I0 + bq * csize;
+              v[u] = x >= total ? 0.0
+                     : q <= I   ? upart[((size_t)I * nbmax + q) * 32 + l]
+                                : tpart[((size_t)(q - 1) * nbmax + I) * 32 + l];
+            }
+#pragma unroll
+            for (int u = 0; u < kEStage; ++u)
+              if (x0 + u * NT < total) stg[x0 + u * NT] = v[u];
+          }
+          __syncthreads();
+          if (warp < nrow) {
+            const int i = base + 32 * (I0 + warp * csize) + lane;
+            const double* sp = stg + warp * e_per + lane;
+            double p = sp[0];
+            for (int q = 1; q <= nb; ++q) p += sp[q * 32];
+            if (i < m) put_p(i, p);
+          }
+          __syncthreads();
+        }
+      } else {
+        for (int i = base + crank * NT + tid; i < m; i += GW * 32) {
+          const int r = i - base, I = r >> 5, l = r & 31;
+          double p;
+          if (SMEM) {
+            p = upart[I * 32 + l];
+          } else {
+            const double* up = upart + (size_t)I * nbmax * 32 + l;
+            p = up[0];
+            for (int J = 1; J <= I; ++J) p += up[(size_t)J * 32];
+          }
+          for (int I2 = I; I2 < nb; ++I2) p += tpart[((size_t)I2 * nbmax + I) * 32 + l];
+          put_p(i, p);
         }
       }
       if constexpr (CL) {

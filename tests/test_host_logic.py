@@ -14,6 +14,7 @@ CSRC = os.path.join(ROOT, "paper_2002_04989_gb300", "csrc")
 
 DRIVER = r"""
 #include "host_plan.h"
+#include "tile_split.h"
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -30,6 +31,24 @@ int main(int argc, char** argv) {
     printf("%d %d %d %d\n", p.hybrid ? 1 : 0, p.bulk_grid, p.tail_at, p.tail_grid);
   } else if (!strcmp(argv[1], "cluster")) {
     printf("%d\n", cluster_size_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])));
+  } else if (!strcmp(argv[1], "tsplit")) {
+    // every (nb, GW): the ranges partition the tiles in order, and no warp takes more
+    // than the mean plus one tile
+    double worst = 0.0;
+    for (int nb = 1; nb <= 130; ++nb)
+      for (int GW : {1, 2, 3, 4, 8, 12, 16, 24, 48, 96, 128, 192, 256, 608, 912, 1216, 2432}) {
+        const int T = nb * (nb + 1) / 2;
+        if (tile_start(0, nb, GW) != 0 || tile_start(GW, nb, GW) != T) { printf("BAD ends %d %d\n", nb, GW); return 1; }
+        const double mean = (double)T / GW;
+        for (int w = 0; w < GW; ++w) {
+          const int a = tile_start(w, nb, GW), b = tile_start(w + 1, nb, GW);
+          if (b < a) { printf("BAD order %d %d %d\n", nb, GW, w); return 1; }
+          const double c = b - a;
+          if (c > mean + 1.0 + 1e-9) { printf("BAD balance %d %d %d %f %f\n", nb, GW, w, c, mean); return 1; }
+          worst = std::max(worst, c - mean);
+        }
+      }
+    printf("ok %.3f\n", worst);
   } else if (!strcmp(argv[1], "group")) {
     printf("%d\n", group_size_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])));
   } else if (!strcmp(argv[1], "crounds")) {
@@ -199,6 +218,11 @@ def test_cluster_plan(driver):
             assert k == 16 or nt * 2 * k > sms       # the largest such power of two
         else:
             assert 2 * nt > sms
+
+
+def test_tile_split_partitions_and_balances(driver):
+    out = driver("tsplit")
+    assert out[0] == "ok", out
 
 
 def test_group_plan(driver):
