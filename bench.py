@@ -47,16 +47,22 @@ TRIDIAG_FLOPS = 4.0 / 3.0 * (N ** 3 + N * (N - 1) ** 3)
 # DRAM traffic of the tridiagonalisation phase of one step (all its launches), from an
 # ncu capture scaled by the work (profiles/), valid only while the kernel's device code
 # is unchanged: sha256 of csrc/tridiag.cu up to the end of its anonymous namespace,
-# which holds every device function (host-side launch code below it may change).
+# which holds every device function (host-side launch code below it may change),
+# followed by the header of the tile split it includes.
 TRIDIAG_TRAFFIC = {"bytes_per_launch": 3.195e12,
-                   "device_code_sha256": "8dc7ab01ead8c315d5516715953e4f458d5dc6e9d1ff00f40b74d86808bcb1a6"}
+                   "device_code_sha256": "b84837d136f53d46e99992a4bf92b5a4536df4b81a4293ef54d3b6875fe4c778"}
 
 
-def device_code_sha(path: str) -> str:
-    """sha256 of a kernel source up to the end of its anonymous namespace (the device code)."""
+def device_code_sha(path: str, *headers: str) -> str:
+    """sha256 of a kernel source up to the end of its anonymous namespace (the device code)
+    and of the headers given."""
     with open(path) as f:
         text = f.read()
-    return hashlib.sha256(text[: text.index("}  // namespace\n")].encode()).hexdigest()
+    text = text[: text.index("}  // namespace\n")]
+    for h in headers:
+        with open(h) as f:
+            text += f.read()
+    return hashlib.sha256(text.encode()).hexdigest()
 
 
 def dist_env():
@@ -282,7 +288,8 @@ def run_gpu(args, world, rank, local):
     tri_avg = statistics.mean(tri_ms)
     achieved = TRIDIAG_FLOPS / (tri_avg / 1e3) / 1e12
     peak = FP64_PEAK_GFLOPS / 1e3
-    sha = device_code_sha(os.path.join(ROOT, "paper_2002_04989_gb300", "csrc", "tridiag.cu"))
+    csrc = os.path.join(ROOT, "paper_2002_04989_gb300", "csrc")
+    sha = device_code_sha(os.path.join(csrc, "tridiag.cu"), os.path.join(csrc, "tile_split.h"))
     traffic = (TRIDIAG_TRAFFIC["bytes_per_launch"]
                if TRIDIAG_TRAFFIC["device_code_sha256"] == sha else None)
     phase_avg = {k: round(statistics.mean(ph[k] for ph in phases), 3) for k in phases[0]}

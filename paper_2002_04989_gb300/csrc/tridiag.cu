@@ -586,13 +586,16 @@ __global__ void __launch_bounds__(W * 32, (MinBlocks<SMEM, W, HI>::value)) k_tri
           wC[i] = p * tau;
         }
       };
-      // Split variants (short steps): the block-rows I = crank, crank + csize, ... are
-      // taken RB at a time; all threads first stage the nb + 1 partials of each of their
-      // elements in shared memory (the tile scratch, idle now), kEStage loads in flight a
-      // thread, and one warp per block-row then adds them from there.
+      // Split variants whose CTAs hold few block-rows each (short steps): all threads first
+      // stage the nb + 1 partials of each element of the CTA's block-rows I = crank,
+      // crank + csize, ... in shared memory (the tile scratch, idle now), kEStage loads in
+      // flight a thread, and one warp per block-row then adds them from there.  With more
+      // block-rows than the scratch holds at once, the plain loop below is faster (the
+      // staged sums would run on few warps in several rounds).
       const int e_per = (nb + 1) * 32;
       const int e_rb = (W * kTile * kTilePad) / e_per;
-      if ((CL || GR) && !SMEM && e_rb >= 1) {
+      const int e_rows = (nb + csize - 1) / csize;
+      if ((CL || GR) && !SMEM && e_rb >= 1 && e_rows <= e_rb && e_rows <= W) {
         double* stg = scal + 8;
         const int RB = e_rb < W ? e_rb : W;
         for (int I0 = crank; I0 < nb; I0 += RB * csize) {
