@@ -68,6 +68,29 @@ __device__ __forceinline__ double warp_dot(const double* x, const double* y, int
   return warp_sum((q0 + q1) + (q2 + q3));
 }
 
+// Row half of a ragged off-diagonal tile with nrows <= 32/P rows inside the matrix (global
+// variants; the tile is in the warp's shared copy, every column valid): lane l takes row
+// l mod (32/P) and the P-th part (l / (32/P)) of the columns, one chain each, and the
+// parts are added by shuffles in a fixed order; lane r < 32/P ends with row r's partial
+// (the other lanes with 0).
+template <int P>
+__device__ __forceinline__ void row_half_split(const double* tile, const double* vC, int C0,
+                                               int lane, int nrows, double (&u)[4]) {
+  constexpr int TP = 33, R = 32 / P, CW = 32 / P;
+  const int r = lane & (R - 1), part = lane / R;
+  const double* rowp = tile + r * TP + part * CW;
+  const double* vp = vC + C0 + part * CW;
+  double acc = 0.0;
+#pragma unroll
+  for (int cc = 0; cc < CW; ++cc) {
+    const double x = r < nrows ? rowp[cc] : 0.0;
+    acc = fma(x, vp[cc], acc);
+  }
+#pragma unroll
+  for (int o = 16; o >= R; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  u[0] += lane < R ? acc : 0.0;
+}
+
 // One 32x32 tile of the fused pass: rows [R0, R0+32), columns [C0, C0+32) of the
 // working matrix.  Lane l owns column C0+l in the column half and row R0+l in the
 // row half.  EDGE tiles (on the diagonal, or with rows beyond m) use predicated
@@ -148,6 +171,21 @@ __device__ __forceinline__ void tile_step(double* S, int64_t ld, int m, int R0, 
   // with 16 warps on the SM a warp gets an FP64 issue slot only every few hundred
   // cycles, so the chain's latency is hidden and no per-tile combine is needed.
   constexpr int NCH = SMEM ? 4 : 1;
+  if constexpr (!SMEM && EDGE) {
+    // A ragged tile of the global variants (J < I, rows past m): with at most 16 (8)
+    // rows left, 2 (4) lanes share each row and take a half (quarter) of the columns
+    // each, so no FP64 instruction runs with most lanes masked; shuffles add the parts.
+    if (nrows <= 8) {
+      row_half_split<4>(tile, vC, C0, lane, nrows, u);
+      __syncwarp();
+      return;
+    }
+    if (nrows <= 16) {
+      row_half_split<2>(tile, vC, C0, lane, nrows, u);
+      __syncwarp();
+      return;
+    }
+  }
   const int i = R0 + lane;
   const int ir = EDGE ? min(i, m - 1) : i;   // clamped row address for the shared copy
   const double* rowp = SMEM ? (S + (size_t)ir * ld + C0) : (tile + lane * TP);
@@ -175,6 +213,9 @@ __device__ __forceinline__ void diag_tile(double* S, int64_t ld, int m, int R0, 
   const int nrows = min(32, m - R0);   // rows (= columns) of the tile inside the matrix
 #pragma unroll
   for (int it = 0; it < 17; ++it) {
+    // a ragged tile skips the warp-rows whose rows all lie past m (warp-uniform): the
+    // first row of warp-row it is it (it < 16) or 31
+    if ((it < 16 ? it : 31) >= nrows) continue;
     int i, c;
     bool valid;
     if (it < 15) {
@@ -209,7 +250,8 @@ __device__ __forceinline__ void diag_tile(double* S, int64_t ld, int m, int R0, 
   const int i = lane;
 #pragma unroll
   for (int cc = 0; cc < 32; ++cc) {
-    const bool ok = i < nrows && cc < nrows;
+    if (cc >= nrows) break;   // columns past m add nothing (warp-uniform)
+    const bool ok = i < nrows;
     const double x = ok ? tile[i * TP + cc] : 0.0;
     u[0] = fma(x, vC[R0 + cc], u[0]);   // one chain (global variant, see tile_step)
   }
