@@ -1060,7 +1060,7 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
   cudaDeviceProp prop;
   EEID_CK(cudaGetDeviceProperties(&prop, ctx->device), "cudaGetDeviceProperties");
   char header[384];
-  snprintf(header, sizeof header, "eeid-tune v2 sms=%d name=%s", prop.multiProcessorCount, prop.name);
+  snprintf(header, sizeof header, "eeid-tune v3 sms=%d name=%s", prop.multiProcessorCount, prop.name);
   const int mmax = std::min(max_m, 1024);
   std::vector<eeid_ctx::Rule> chosen;
   // ---- cached table
@@ -1087,7 +1087,9 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
       chosen.clear();
     }
   }
-  // ---- measure: for each bucket, every supported variant on a full wave of minors
+  // ---- measure: for each bucket, every supported variant on a wave of minors whose sizes
+  // cover the bucket evenly (as a batch of uneven matrices does), long enough (about
+  // 1.5e11 flops, at least two tasks per SM) that the last partial round weighs little
   static const int kBuckets[] = {16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 384, 512, 768, 1024};
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1105,9 +1107,12 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
     if (prev >= mmax) break;
     const int m = std::min(bm, mmax);
     const int n = m + 1;
-    const double flops_task = 4.0 / 3.0 * (double)m * m * m;
+    const int lo = prev + 1;   // minor sizes lo..m
+    double flops_task = 0.0;
+    for (int q = lo; q <= m; ++q) flops_task += 4.0 / 3.0 * (double)q * q * q;
+    flops_task /= (double)(m - lo + 1);
     const int T = (int)std::max<double>(2.0 * ctx->sms,
-                                        std::min<double>(64.0 * ctx->sms, 3e10 / flops_task));
+                                        std::min<double>(64.0 * ctx->sms, 1.5e11 / flops_task));
     struct Cand { TriCfg c; int grid; size_t slot; };
     std::vector<Cand> cands;
     for (int path = 0; path < 3; ++path)
@@ -1132,7 +1137,8 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
     std::vector<TridiagTask> tasks(T);
     for (int t = 0; t < T; ++t) {
       double* d = (double*)(ws + de_off) + (size_t)t * 2 * m;
-      tasks[t] = {A, n, n, t % n, d, d + m};
+      const int nt = lo + 1 + t % (m - lo + 1);   // leading nt x nt block; minor size nt - 1
+      tasks[t] = {A, n, nt, t % nt, d, d + m};
     }
     ce = launch_fill_symmetric(A, n, n, 0x5eedULL + (unsigned long long)m, s);
     if (ce == cudaSuccess)

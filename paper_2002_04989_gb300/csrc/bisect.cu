@@ -36,7 +36,9 @@
 //    the Gershgorin bracket, so the result never depends on the FP32 phase.
 //  * The two verifying counts also return det(T - xI) at the bracket ends; one
 //    secant step and two counts around it cut the FP64 finish from about 13
-//    halvings to 1-3 (verified by counts; bisection is the fallback).
+//    halvings to none: when the counts put eigenvalue k inside the window
+//    x1 +- h, h = max(2^-50 |x1|, 2^-51 ||T||), the lane returns x1, verified to h
+//    (bisection from the narrowed bracket is the fallback).
 #include "internal.cuh"
 
 namespace eeid {
@@ -349,6 +351,10 @@ k_bisect(const BisectTask* __restrict__ tasks, const BisectItem* __restrict__ it
         if (hi > b) {
           if (sturm_count(de, m, b) > k) hi = b; else lo = b;
         }
+        // both window counts held: eigenvalue k is in (a, b], and its midpoint is the
+        // secant estimate, accurate to the FP64 values' rounding; no halving refines it
+        // further in any useful way, so the lane is done (verified to +-h)
+        if (lo == a && hi == b) active = false;
       }
     }
   }

@@ -319,7 +319,7 @@ def test_autotune_table_and_cache(torch_cuda, tmp_path, oracle_mod):
     try:
         c1.eeid_autotune(256, path)
         lines = open(path).read().splitlines()
-        assert lines[0].startswith("eeid-tune v2") and len(lines) > 3
+        assert lines[0].startswith("eeid-tune v3") and len(lines) > 3
         assert int(lines[-1].split()[1]) >= 256
         c2.eeid_autotune(256, path)              # loads the cached table
         o1 = c1.eeid_components(dev(torch_cuda, A)).cpu().numpy()
@@ -393,12 +393,12 @@ def test_autotune_rejects_foreign_cache(torch_cuda, tmp_path):
     """A cache written for another device model is ignored (re-tuned and rewritten)."""
     from paper_2002_04989_gb300 import eeid
     path = tmp_path / "tune.txt"
-    path.write_text("eeid-tune v2 sms=1 name=Some Other GPU\n1 4096 1 4\n")
+    path.write_text("eeid-tune v3 sms=1 name=Some Other GPU\n1 4096 1 4\n")
     c = eeid.Context(0)
     try:
         c.eeid_autotune(64, str(path))
         head = path.read_text().splitlines()[0]
-        assert "Some Other GPU" not in head and head.startswith("eeid-tune v2")
+        assert "Some Other GPU" not in head and head.startswith("eeid-tune v3")
     finally:
         c.close()
 
