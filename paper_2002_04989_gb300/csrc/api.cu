@@ -193,7 +193,8 @@ bool cfg_supported(int path, int warps, int m) {
   bool ok;
   if (path == 0) ok = (warps == 1 || warps == 2 || warps == 4 || warps == 8) && m <= kTridiagSmemMaxM;
   else if (path == 1)
-    ok = (warps == 2 || warps == 4 || warps == 8 || warps == 12 || warps == 16) && m <= kTridiagMaxM;
+    ok = (warps == 1 || warps == 2 || warps == 4 || warps == 8 || warps == 12 || warps == 16) &&
+         m <= kTridiagMaxM;
   else if (path == 2) ok = (warps == 4 || warps == 8) && m <= kTridiagMaxM;
   else ok = false;
   return ok && tridiag_smem_bytes(path == 0, m, warps) <= kMaxSmemPerBlock;
@@ -1088,7 +1089,7 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
     }
   }
   // ---- measure: for each bucket, every supported variant on a wave of minors whose sizes
-  // cover the bucket evenly (as a batch of uneven matrices does), long enough (about
+  // cover the bucket evenly, largest first (as a batch of uneven matrices does), long enough (about
   // 1.5e11 flops, at least two tasks per SM) that the last partial round weighs little
   static const int kBuckets[] = {16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 384, 512, 768, 1024};
   cudaStream_t s = nullptr;
@@ -1137,7 +1138,9 @@ eeid_status eeid_autotune(eeid_ctx* ctx, int max_m, const char* cache_path) {
     std::vector<TridiagTask> tasks(T);
     for (int t = 0; t < T; ++t) {
       double* d = (double*)(ws + de_off) + (size_t)t * 2 * m;
-      const int nt = lo + 1 + t % (m - lo + 1);   // leading nt x nt block; minor size nt - 1
+      // leading nt x nt block (minor size nt - 1), largest first like a real batch's
+      // cost-sorted task list
+      const int nt = m + 1 - (int)((int64_t)t * (m - lo + 1) / T);
       tasks[t] = {A, n, nt, t % nt, d, d + m};
     }
     ce = launch_fill_symmetric(A, n, n, 0x5eedULL + (unsigned long long)m, s);

@@ -352,7 +352,8 @@ constexpr int kEStage = 8;
 template <bool SMEM, int W, bool HI = false>
 struct MinBlocks {
   static constexpr int value = HI ? ((W >= 8) ? 3 : 6)
-                                  : (W >= 12) ? 1 : (W >= 8) ? 2 : (SMEM && W <= 2) ? 8 : 4;
+                                  : (W >= 12) ? 1 : (W >= 8) ? 2 : (SMEM && W <= 2) ? 8
+                                  : (!SMEM && W == 1) ? 16 : (!SMEM && W == 2) ? 8 : 4;
 };
 
 // CL = true: the cluster variant (global-slot path only).  One thread-block cluster of C
@@ -784,6 +785,7 @@ cudaError_t launch_tridiag(bool smem_path, int warps, int grid, const TridiagLau
     }
   } else {
     switch (warps) {
+      case 1: return launch_one<false, 1>(grid, L, s);
       case 2: return launch_one<false, 2>(grid, L, s);
       case 4: return launch_one<false, 4>(grid, L, s);
       case 8: return launch_one<false, 8>(grid, L, s);
@@ -959,7 +961,8 @@ cudaError_t preload_tridiag() {
 #define EEID_PRE(S_, W_) \
   if (e == cudaSuccess) e = raise_smem_limit_once((const void*)k_tridiag<S_, W_>, smem_limit_set<S_, W_>());
   EEID_PRE(true, 1) EEID_PRE(true, 2) EEID_PRE(true, 4) EEID_PRE(true, 8)
-  EEID_PRE(false, 2) EEID_PRE(false, 4) EEID_PRE(false, 8) EEID_PRE(false, 12) EEID_PRE(false, 16)
+  EEID_PRE(false, 1) EEID_PRE(false, 2) EEID_PRE(false, 4) EEID_PRE(false, 8) EEID_PRE(false, 12)
+  EEID_PRE(false, 16)
 #undef EEID_PRE
   if (e == cudaSuccess)
     e = raise_smem_limit_once((const void*)k_tridiag<false, 4, false, true>, smem_limit_set<false, 204>());
@@ -1000,7 +1003,8 @@ int tridiag_blocks_per_sm(bool smem_path, int warps, int max_m, bool hi) {
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tridiag<S_, W_>, W_ * 32, smem); \
   }
   EEID_OCC(true, 1) EEID_OCC(true, 2) EEID_OCC(true, 4) EEID_OCC(true, 8)
-  EEID_OCC(false, 2) EEID_OCC(false, 4) EEID_OCC(false, 8) EEID_OCC(false, 12) EEID_OCC(false, 16)
+  EEID_OCC(false, 1) EEID_OCC(false, 2) EEID_OCC(false, 4) EEID_OCC(false, 8) EEID_OCC(false, 12)
+  EEID_OCC(false, 16)
 #undef EEID_OCC
   return e == cudaSuccess ? nb : 0;
 }
