@@ -237,8 +237,10 @@ int64_t eeid_vector_refs(const eeid_ctx* ctx);
  * m <= 160; 1 = working matrix in a global-memory slot per CTA; 2 = the global-slot
  * variant built for high occupancy, at most 80 registers a thread so that three 8-warp
  * or six 4-warp CTAs share an SM) with `warps` warps per CTA (path 0: 1, 2, 4, 8;
- * path 1: 2, 4, 8, 12, 16; path 2: 4, 8).  Paths 1 and 2 run the same arithmetic.
- * Later rules take precedence.
+ * path 1: 1, 2, 4, 8, 12, 16, where 1 and 2 are built for 16 and 8 CTAs per SM; path
+ * 2: 4, 8).  Paths 1 and 2 run the same arithmetic.  Later rules take precedence.  A
+ * call whose group of such matrices is too small to fill the SMs with a 1- or 2-warp
+ * choice runs them with 4 warps instead (same results).
  * The warp count never changes a result: every instantiation of one path sums in
  * the same order, so the two paths' results are each bitwise fixed by m.  Changing
  * the path of a size changes the rounding order (not the accuracy class).  A rule
@@ -252,9 +254,10 @@ eeid_status eeid_tune_reset(eeid_ctx* ctx);
 
 /* Autotuner for the Householder kernel.  For size buckets up to min(max_m, 1024)
  * it times every supported variant (shared-memory or global-slot working matrix,
- * 1-16 warps per CTA, both builds of the global slot) on a full wave of synthetic m x m minors on this device,
- * keeps the fastest per bucket, and installs the choices as tuning rules (larger
- * sizes keep the built-in choice).  With `cache_path` non-NULL the table is read
+ * 1-16 warps per CTA, both builds of the global slot) on this device, on a wave of
+ * synthetic minors whose sizes cover the bucket, largest first (as in a batch), keeps
+ * the fastest per bucket, and installs the choices as tuning rules (larger sizes keep
+ * the built-in choice).  With `cache_path` non-NULL the table is read
  * from that file when it exists and was made on the same device model, and
  * written there after tuning.  Runs synchronously on an internal stream; takes a
  * few seconds.  Errors: EEID_ERR_CUDA, EEID_ERR_NOMEM (workspace budget). */
