@@ -455,11 +455,9 @@ eeid_status run(eeid_ctx* ctx, std::vector<Problem>& probs, Mode mode, cudaStrea
     g.max_m = tri[g.idx[0]].m;
     g.cfg = key >= 96 ? herm_cfg(g.max_m) : tri_cfg(ctx, g.max_m);
     const int sms_used = std::max(1, ctx->sms - ctx->sm_reserve);
-    // The narrow global builds (1 or 2 warps, many CTAs per SM) win only on waves that
-    // fill the SMs with them; a group of fewer matrices runs 4 warps a matrix instead
-    // (every global build gives the same bits).
+    // a narrow global build only for a wave that fills the SMs with it (narrow_build_fills)
     if (!g.cfg.smem && !g.cfg.herm && g.cfg.warps < 4 &&
-        (int64_t)g.idx.size() * 2 < (int64_t)sms_used * blocks_per_sm(ctx, g.cfg, g.max_m))
+        !narrow_build_fills((int64_t)g.idx.size(), sms_used, blocks_per_sm(ctx, g.cfg, g.max_m)))
       g.cfg = TriCfg{false, 4};
     const int bps = blocks_per_sm(ctx, g.cfg, g.max_m);
     g.grid = (int)std::min<int64_t>((int64_t)g.idx.size(), (int64_t)sms_used * bps);

@@ -86,6 +86,14 @@ inline int cluster_size_for(int nt, int sms, int max_m, int min_m = kClusterMinM
   return c >= 2 ? c : 0;
 }
 
+// The narrow global builds of K-a (1 or 2 warps a matrix, 16 or 8 CTAs per SM) win only
+// on waves that fill the SMs with them: a group keeps such a build only when it holds at
+// least half the SMs' worth of its CTAs (nt * 2 >= sms * blocks_per_sm), and otherwise
+// runs 4 warps a matrix (every global build gives the same bits).
+inline bool narrow_build_fills(int64_t nt, int sms, int blocks_per_sm) {
+  return nt * 2 >= (int64_t)sms * blocks_per_sm;
+}
+
 // Group plan (the group variant): when even clusters of 16 would leave most SMs idle (a
 // call with a handful of large reductions, e.g. one component of a large A: A and one
 // minor), G = sms / nt CTAs reduce each matrix, resident together through a cooperative

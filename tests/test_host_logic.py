@@ -49,6 +49,8 @@ int main(int argc, char** argv) {
         }
       }
     printf("ok %.3f\n", worst);
+  } else if (!strcmp(argv[1], "narrow")) {
+    printf("%d\n", narrow_build_fills(atoll(argv[2]), atoi(argv[3]), atoi(argv[4])) ? 1 : 0);
   } else if (!strcmp(argv[1], "group")) {
     printf("%d\n", group_size_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])));
   } else if (!strcmp(argv[1], "crounds")) {
@@ -223,6 +225,17 @@ def test_cluster_plan(driver):
 def test_tile_split_partitions_and_balances(driver):
     out = driver("tsplit")
     assert out[0] == "ok", out
+
+
+def test_narrow_builds_only_on_full_waves(driver):
+    f = lambda nt, sms=152, bps=16: driver("narrow", nt, sms, bps)[0] == "1"
+    # a six-copy batch at n = 300 (1806 reductions) fills the 1-warp build's 2432 slots
+    # at least half; a single n = 300 call (301 reductions) does not
+    assert f(1806) and not f(301)
+    # the 2-warp build (8 CTAs per SM): the boundary is half of 1216 slots
+    assert f(608, bps=8) and not f(607, bps=8)
+    # batch4096's (192, 256] slice: 316 matrices, about 71k reductions
+    assert f(71000, bps=8)
 
 
 def test_group_plan(driver):
